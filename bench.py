@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""RK45 cell-steps/s of the micromagnetic hot path on GB300.
+
+One step = one accepted Dormand-Prince RK45 step of the whole path (demag FFT
+convolution, exchange stencil, anisotropy, Zeeman, LL torque, stage updates,
+error reduction and step control) over the whole grid.
+
+Default workload: the 3-D ellipsoid, 128 x 128 x 32 cells of 3 nm (demag
+convolution padded to 256 x 256 x 64), the configuration on which both the
+cell-steps/s and the HBM-roofline fraction of the demag convolution are
+quoted; the 256 x 256 x 1 grain film is reported beside it ("film").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the path does not shard (one simulation per GPU); N ranks run N
+independent replicas ("replicas only", weak scaling), no collective on the
+data path.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1406_7635_gb300.workloads import WORKLOADS  # noqa: E402
+
+METRIC = "RK45 cell-steps/s at 256²×1 and 128²×32; demag FFT-conv % of HBM roofline"
+DEFAULT_WORKLOAD = "ellipsoid_128x128x32"
+SIDE_WORKLOAD = "grains_256x256x1"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_demag_bytes(p):
+    """Minimum HBM bytes of one demag convolution: read m (3 x 4 B) and the
+    mask/region bytes (2 B) per cell, the kernel spectrum octant (6 float32 per
+    octant point), write B (3 x 4 B) per cell."""
+    def half(n):
+        return 1 if n == 1 else (1 << (2 * n - 2).bit_length()) // 2 + 1
+    octant = half(p.nx) * half(p.ny) * half(p.nz)
+    return p.ncells * (12 + 2 + 12) + 6 * 4 * octant
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1406_7635_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    build()
+    from paper_1406_7635_gb300 import mm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def bench_workload(name, steps, warmup):
+        p = WORKLOADS[name]()
+        ctx = mm.Context.from_problem(p, device=local_rank, stream=stream.cuda_stream)
+        ctx.step(warmup)
+        s0 = ctx.get_stats()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.zero_()                  # evict the previous step's data from L2
+                starts[k].record(stream)
+                ctx.step(1)
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        dev_s = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3
+        s1 = ctx.get_stats()
+        return p, ctx, dev_s, s0, s1, clk
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    K, W = args.steps, args.warmup
+    p, ctx, dev_s, s0, s1, clk = bench_workload(args.workload, K, W)
+    t_max = reduce_max(dev_s)
+    value = p.ncells * K * world / t_max
+    attempts = (s1["accepted"] + s1["rejected"]) - (s0["accepted"] + s0["rejected"])
+    launches = s1["launches"] - s0["launches"]
+
+    # demag convolution alone (the dominant kernel sequence), events on the
+    # context's stream, L2 flushed before each launch
+    m_dev = torch.tensor(p.m0.astype(np.float32), device=dev).contiguous()
+    b_dev = torch.empty_like(m_dev)
+    R = 50
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+    for _ in range(3):
+        ctx.demag_apply(m_dev, b_dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            ctx.demag_apply(m_dev, b_dev)
+            b.record(stream)
+    torch.cuda.synchronize()
+    conv_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / R
+    peaks, peak_kind = measured_peaks()
+    alg = algorithmic_demag_bytes(p)
+    achieved = alg / conv_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", f"demag_conv_{args.workload}.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("dram_bytes_per_conv")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": "demag FFT convolution (x R2C, y, z*K*z^-1, y^-1, x C2R passes)",
+                "algorithmic_bytes": alg, "avg_launch_us": round(conv_s * 1e6, 2), "peak_kind": peak_kind}
+
+    # end to end through the C ABI with host buffers: m up, one step, m down
+    Ke = min(K, 50)
+    host_m = ctx.get_m()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        ctx.set_m(host_m)
+        ctx.step(1)
+        host_m = ctx.get_m()
+    e2e_s = reduce_max(time.perf_counter() - t0)
+    e2e = {"value": p.ncells * Ke * world / e2e_s, "unit": "cell-steps/s",
+           "h2d_bytes_per_step": 3 * 4 * p.ncells, "d2h_bytes_per_step": 3 * 4 * p.ncells, "steps": Ke}
+    evals_per_step = 6.0 * attempts / K
+    ctx.close()
+
+    side = None
+    if args.side and args.workload != SIDE_WORKLOAD:
+        ps, cs, ds, a0, a1, _ = bench_workload(SIDE_WORKLOAD, K, W)
+        side = {"workload": SIDE_WORKLOAD, "value": ps.ncells * K * world / reduce_max(ds), "unit": "cell-steps/s",
+                "ms_per_step": ds / K * 1e3}
+        cs.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [p.nx, p.ny, p.nz], "cells": p.ncells,
+                   "cell_m": [p.dx, p.dy, p.dz], "magnetic_cells": int(p.magnetic().sum()),
+                   "max_err": p.max_err, "parallelism": f"replicas{world}",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "evals_per_step": evals_per_step, "rejected_attempts": int(s1["rejected"] - s0["rejected"])},
+        "cell_evals_per_s": value * evals_per_step,
+        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    if side:
+        out["film"] = side
+    return out
+
+
+def oracle_cpu_run(name, budget_s, max_steps):
+    """The float64 oracle on the same workload: kernel set-up untimed, then
+    accepted adaptive RK45 steps until the time budget is spent."""
+    from oracle.rk45 import RK45
+    p = WORKLOADS[name]()
+    s = RK45(p)
+    s.field.torque(s.m, 0.0)          # first stage (untimed, like the GPU's warm-up)
+    s.k1 = s.field.torque(s.m, 0.0)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        s.adaptive_step()
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return p, steps, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    budget = float(os.environ.get("MM_REF_BUDGET_S", 60))
+    p, steps, dt = oracle_cpu_run(args.workload, budget, max(args.steps, 1))
+    v = p.ncells * steps / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "cell-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": 0, "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [p.nx, p.ny, p.nz], "cells": p.ncells},
+        "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} accepted RK45 steps of the full {args.workload} grid "
+                                   f"(float64 numpy oracle, kernel set-up untimed, ~{budget:.0f} s budget)"},
+        "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", dest="side", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = env_rank()
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        budget = float(os.environ.get("MM_CPU_BUDGET_S", 20))
+        p, steps, dt = oracle_cpu_run(args.workload, budget, 1000)
+        out["cpu_baseline"] = {"value": p.ncells * steps / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{steps} accepted RK45 steps of the full {args.workload} grid "
+                                         f"(float64 numpy oracle, kernel set-up untimed)"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

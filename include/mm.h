@@ -1,0 +1,177 @@
+/*
+ * mm.h -- C ABI of the GB300 finite-difference micromagnetics library.
+ *
+ * The library evaluates the effective field of a finite-difference magnet and
+ * advances the Landau-Lifshitz equation with adaptive Dormand-Prince RK45, as
+ * described in "The design and verification of Mumax3" (Vansteenkiste et al.,
+ * AIP Advances 4, 107133, 2014): Sec. II (grid, regions), Sec. III (torque and
+ * effective-field terms), Sec. IV (time integration).
+ *
+ * Conventions for every entry point:
+ *  - Return value: MM_OK (0) or a negative MM_ERR_* code.  mm_last_error()
+ *    returns a NUL-terminated, thread-local message owned by the library that
+ *    describes the last failure on the calling thread.
+ *  - Units are SI: T, A/m, J/m, J/m^3, s, m.
+ *  - Spatial arrays are cell-centred, x fastest: index (z*ny + y)*nx + x.
+ *    Vector arrays are structure-of-arrays float32 [3][nz][ny][nx] (component
+ *    planes x, y, z).  Byte maps (geometry, regions) are uint8 [nz][ny][nx].
+ *  - Host pointers are read or written only during the call; the library never
+ *    keeps them.  *_device variants take device pointers on the context's
+ *    device; they are ordered on the context's stream and the call returns once
+ *    the stream has finished with them.
+ *  - A context owns all device memory it allocates and releases it in
+ *    mm_destroy.  A context is not thread-safe: one thread at a time.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MM_OK = 0,
+  MM_ERR_ARG = -1,          /* bad size, index, pointer or parameter           */
+  MM_ERR_CUDA = -2,         /* a CUDA runtime call failed                      */
+  MM_ERR_OOM = -3,          /* device allocation failed                        */
+  MM_ERR_NONFINITE = -4,    /* NaN/Inf in the step error (and hence in m)      */
+  MM_ERR_DT_UNDERFLOW = -5, /* a rejected step asked for dt below dt_min      */
+  MM_ERR_TIMEOUT = -6,      /* a bounded device-side wait expired              */
+  MM_ERR_STATE = -7         /* call out of order (e.g. stepping before set_m)  */
+};
+
+typedef struct mm_ctx mm_ctx;
+
+/* Per-region material (Sec. II.A: 256-entry look-up tables by region index). */
+typedef struct {
+  double msat;      /* saturation magnetisation Msat (A/m); 0 = non-magnetic  */
+  double aex;       /* exchange stiffness Aex (J/m), Eq. for B_exch           */
+  double alpha;     /* damping, Eq. eqLLG                                     */
+  double gamma_ll;  /* gyromagnetic ratio (rad/(T s)); 1.7595e11 by default    */
+  double ku1, ku2;  /* uniaxial anisotropy constants (J/m^3), Sec. III.E      */
+  double anis_u[3]; /* anisotropy axis (normalised by the library)            */
+} mm_material;
+
+typedef struct {
+  double total, demag, exch, anis, zeeman; /* J */
+  double m_avg[3];                         /* average m over magnetic cells */
+} mm_energies;
+
+typedef struct {
+  long long accepted;  /* accepted RK45 steps since creation                  */
+  long long rejected;  /* rejected attempts                                   */
+  long long evals;     /* torque evaluations (the paper's Neval)              */
+  double last_err;     /* error estimate of the last attempt                  */
+  double t, dt;        /* current time and the controller's proposed step     */
+  long long launches;  /* kernels this context has launched (host count,      */
+                       /* including graph nodes and no-op tail launches)      */
+} mm_stats;
+
+/* Message of the last failure on this thread ("" if none). */
+const char* mm_last_error(void);
+
+/* Grid of nx*ny*nz orthorhombic cells of dx*dy*dz metres (Sec. II.A; the
+ * script calls setgridsize/setcellsize).  Allocates the state, computes the
+ * demagnetising kernel on the device (Sec. III.B "Magnetostatic kernel") and
+ * sets defaults: every cell in the geometry and in region 0, all materials
+ * zero except gamma_ll = 1.7595e11, all terms enabled, MaxErr 1e-5, headroom
+ * 0.8 (Sec. IV).  cuda_stream is a cudaStream_t on `device`, or NULL for a
+ * stream owned by the context.  *out is NULL on failure. */
+int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
+              double dz, int device, void* cuda_stream);
+/* Releases the context and its device memory; NULL is accepted. */
+int mm_destroy(mm_ctx* ctx);
+
+/* Geometry mask (Sec. II.B): nonzero = magnet, 0 = vacuum.  NULL = all cells.
+ * Vacuum cells carry m = 0, no torque, and drop out of the exchange sum. */
+int mm_set_geometry(mm_ctx* ctx, const uint8_t* mask);
+/* Region index per cell, 0..255 (Sec. II.A).  NULL = all region 0. */
+int mm_set_regions(mm_ctx* ctx, const uint8_t* region);
+/* Material of one region (0..255). */
+int mm_set_region_material(mm_ctx* ctx, int region, const mm_material* mat);
+/* Exchange scale S between two regions (Eq. for inter-region exchange,
+ * symmetric, default 1). */
+int mm_set_exchange_scale(mm_ctx* ctx, int r1, int r2, double S);
+/* Applied field B_ext(region, t) = b0 + b1 sin(2 pi freq t + phase) (Sec. II.A
+ * "Excitations": one function of time times a per-region profile).  region -1
+ * sets every region.  b1 may be NULL (static field). */
+int mm_set_bext(mm_ctx* ctx, int region, const double b0[3], const double b1[3]);
+int mm_set_bext_timefn(mm_ctx* ctx, double freq, double phase);
+/* Enables the demag, exchange, anisotropy and Zeeman terms and the precession
+ * term of Eq. eqLLG (precession off = relaxation dynamics). */
+int mm_enable_terms(mm_ctx* ctx, int demag, int exch, int anis, int zeeman,
+                    int precession);
+
+/* Reduced magnetisation m, float32 SoA [3][nz][ny][nx].  The library
+ * normalises it per magnetic cell and zeroes it in vacuum.  Setting m
+ * invalidates the cached first RK stage. */
+int mm_set_m(mm_ctx* ctx, const float* m);
+int mm_get_m(mm_ctx* ctx, float* m);
+int mm_set_m_device(mm_ctx* ctx, const float* dm);
+int mm_get_m_device(mm_ctx* ctx, float* dm);
+
+/* Adaptive step control (Sec. IV): MaxErr (default 1e-5), headroom (0.8),
+ * initial step dt0 and the bounds dt_min, dt_max (s). */
+int mm_set_solver(mm_ctx* ctx, double max_err, double headroom, double dt0,
+                  double dt_min, double dt_max);
+/* Replay mode: the next steps take exactly dts[0..n-1] and are all accepted
+ * (the error is still computed and reported).  n = 0 returns to adaptive
+ * stepping.  The array is copied. */
+int mm_set_fixed_dt_sequence(mm_ctx* ctx, const double* dts, int n);
+
+/* Takes n accepted RK45 steps (the paper's steps(n)).  In replay mode takes
+ * min(n, remaining) steps. */
+int mm_step(mm_ctx* ctx, int n);
+/* Advances to t_end exactly (the paper's run(t)); the last step is shortened
+ * to land on t_end.  Returns MM_OK immediately if t >= t_end. */
+int mm_run(mm_ctx* ctx, double t_end);
+
+int mm_get_time(mm_ctx* ctx, double* t, double* dt);
+int mm_set_time(mm_ctx* ctx, double t, double dt);
+
+/* Effective field, demag field and torque (dm/dt) at the current m and t,
+ * float32 SoA [3][nz][ny][nx].  B_eff and the torque are zero in vacuum; the
+ * demag field is the convolution result in every cell (stray field). */
+int mm_get_beff(mm_ctx* ctx, float* b);
+int mm_get_bdemag(mm_ctx* ctx, float* b);
+int mm_get_torque(mm_ctx* ctx, float* tau);
+/* Energies from the effective field with float64 accumulation (Sec. III:
+ * -1/2 M.B_demag, -1/2 M.B_exch, -1/2 B(Ku1).M - 1/4 B(Ku2).M, -M.B_ext). */
+int mm_get_energies(mm_ctx* ctx, mm_energies* e);
+int mm_get_stats(mm_ctx* ctx, mm_stats* s);
+/* Sizes of the accepted steps since creation (up to `max` of them, oldest
+ * first; the library keeps the first 1<<20); *n receives the count copied. */
+int mm_get_dt_history(mm_ctx* ctx, double* dts, int max, int* n);
+
+/* Checkpoint: the full integrator state (m, the cached first stage, t, dt,
+ * controller settings, counters) as an opaque byte blob; resume is bit-exact.
+ * A replay sequence (mm_set_fixed_dt_sequence) is not part of it: restoring
+ * returns to adaptive stepping.  The blob is tied to the grid size. */
+size_t mm_state_bytes(mm_ctx* ctx);
+int mm_get_state(mm_ctx* ctx, void* buf, size_t bytes);
+int mm_set_state(mm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Cell-averaged demagnetising tensor (Sec. III.B "Magnetostatic kernel") of
+ * two dx*dy*dz cells at n integer offsets offsets[3i..3i+2] = (X, Y, Z) in
+ * cells, computed on `device` in float64: out[6i..6i+5] = Nxx, Nyy, Nzz, Nxy,
+ * Nxz, Nyz with the positive convention (self term of a cube 1/3,
+ * B = -mu0 N M).  Host arrays. */
+int mm_demag_tensor(int device, double dx, double dy, double dz, int n,
+                    const int32_t* offsets, double* out);
+
+/* Demagnetising field alone (Sec. III.B convolution) of the magnetisation
+ * m (device pointer, float32 SoA [3][nz][ny][nx], read as Msat m with the
+ * context's regions and geometry) into b (device pointer, same layout).
+ * Ordered on the context's stream; returns after the stream has finished. */
+int mm_demag_apply(mm_ctx* ctx, const float* m, float* b);
+
+/* Blocks until the context's stream is idle. */
+int mm_sync(mm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

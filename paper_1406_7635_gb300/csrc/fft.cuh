@@ -1,0 +1,171 @@
+// Complex FFT building blocks for the demag convolution (Sec. III.B: the
+// convolution is FFT-accelerated by the convolution theorem).
+//
+// Power-of-two lengths only.  A length-L transform is a sequence of Stockham
+// radix passes (radices 16, 8, 4, 2 -- see radix_of) over pencils held in
+// shared memory; each pass reads every element into registers, synchronises,
+// then writes the butterflies' outputs in place, so no second buffer is needed.
+// Twiddles come from one table W[k] = exp(-2 pi i k / 2048) (k < 2048), built
+// on the host in float64 and rounded once to float32.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mmfft {
+
+constexpr int kTwN = 2048;   // twiddle table length: largest supported L
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by DIR * i  (DIR = -1 forward, +1 inverse)
+template <int DIR>
+__device__ __forceinline__ float2 mul_dir_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// exp(DIR * 2 pi i k / 16) for k = 0..7, as constants
+__device__ __forceinline__ float2 w16(int k, int dir) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+  float c, s;
+  switch (k) {
+    case 0: c = 1.f; s = 0.f; break;
+    case 1: c = c1; s = s1; break;
+    case 2: c = h; s = h; break;
+    case 3: c = s1; s = c1; break;
+    case 4: c = 0.f; s = 1.f; break;
+    case 5: c = -s1; s = c1; break;
+    case 6: c = -h; s = h; break;
+    default: c = -c1; s = s1; break;
+  }
+  return make_float2(c, dir < 0 ? -s : s);
+}
+
+// In-register DFT of length R (R = 1, 2, 4, 8, 16), natural order in and out,
+// by recursive even/odd splitting.
+template <int R, int DIR>
+struct Dft {
+  __device__ __forceinline__ static void run(float2 (&x)[R]) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) { e[i] = x[2 * i]; o[i] = x[2 * i + 1]; }
+    Dft<R / 2, DIR>::run(e);
+    Dft<R / 2, DIR>::run(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const float2 t = (k == 0) ? o[k] : cmul(o[k], w16(k * (16 / R), DIR));
+      x[k] = cadd(e[k], t);
+      x[k + R / 2] = csub(e[k], t);
+    }
+  }
+};
+template <int DIR>
+struct Dft<1, DIR> {
+  __device__ __forceinline__ static void run(float2 (&)[1]) {}
+};
+template <int DIR>
+struct Dft<2, DIR> {
+  __device__ __forceinline__ static void run(float2 (&x)[2]) {
+    const float2 a = x[0];
+    x[0] = cadd(a, x[1]);
+    x[1] = csub(a, x[1]);
+  }
+};
+template <int DIR>
+struct Dft<4, DIR> {
+  __device__ __forceinline__ static void run(float2 (&x)[4]) {
+    const float2 a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
+    const float2 a2 = cadd(x[1], x[3]), a3 = mul_dir_i<DIR>(csub(x[1], x[3]));
+    x[0] = cadd(a0, a2);
+    x[2] = csub(a0, a2);
+    x[1] = cadd(a1, a3);
+    x[3] = csub(a1, a3);
+  }
+};
+
+// Radix of pass `p` for length L: 16s first, then the remainder.
+__host__ __device__ constexpr int radix_of(int L, int p) {
+  int ns = 1, r = 1;
+  for (int i = 0; i <= p; ++i) {
+    const int left = L / ns;
+    r = left >= 16 ? 16 : left;   // left is a power of two
+    ns *= r;
+  }
+  return r;
+}
+__host__ __device__ constexpr int npasses(int L) {
+  int ns = 1, n = 0;
+  while (ns < L) { ns *= radix_of(L, n); ++n; }
+  return n;
+}
+__host__ __device__ constexpr int ns_of(int L, int p) {
+  int ns = 1;
+  for (int i = 0; i < p; ++i) ns *= radix_of(L, i);
+  return ns;
+}
+
+// One Stockham pass of radix R on NP pencils of length L in shared memory:
+// element i of pencil q at s[q * PST + i].  NT threads cooperate; butterfly b
+// belongs to pencil b % NP (consecutive threads -> consecutive pencils, which
+// with PST = L + 1 keeps shared-memory accesses free of bank conflicts).
+template <int L, int R, int NS, int DIR, int NP, int NT, int PST>
+__device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw) {
+  constexpr int NB = L / R;
+  constexpr int TOT = NB * NP;
+  constexpr int PER = (TOT + NT - 1) / NT;
+  float2 v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * NT;
+    if (TOT % NT == 0 || b < TOT) {
+      const int p = b % NP, j = b / NP;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = s[p * PST + j + r * NB];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * NT;
+    if (TOT % NT == 0 || b < TOT) {
+      const int p = b % NP, j = b / NP;
+      const int k = j % NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          // exp(DIR 2 pi i r k / (NS R)) = W[r k (kTwN / (NS R))] (conjugated if DIR > 0)
+          float2 w = __ldg(&tw[(r * k * (kTwN / (NS * R))) & (kTwN - 1)]);
+          if (DIR > 0) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      Dft<R, DIR>::run(v[q]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[p * PST + base + r * NS] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full length-L complex transform of NP shared-memory pencils (in place,
+// natural order).  Caller synchronises before (data written) -- the first pass
+// starts with reads; the last pass ends with __syncthreads().
+template <int L, int DIR, int NP, int NT, int PST, int P = 0, bool DONE = (P >= npasses(L))>
+struct Fft;
+template <int L, int DIR, int NP, int NT, int PST, int P>
+struct Fft<L, DIR, NP, NT, PST, P, false> {
+  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw) {
+    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, PST>(s, tw);
+    Fft<L, DIR, NP, NT, PST, P + 1>::run(s, tw);
+  }
+};
+template <int L, int DIR, int NP, int NT, int PST, int P>
+struct Fft<L, DIR, NP, NT, PST, P, true> {
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__) {}
+};
+
+}  // namespace mmfft

@@ -1,0 +1,739 @@
+// C ABI (include/mm.h): context lifetime, parameters, state transfer, the
+// stepping loop and the getters.
+//
+// The stepping loop: one RK45 attempt (6 stage evaluations + error/controller)
+// is captured once into a CUDA graph and replayed.  The controller runs on the
+// device and marks the call done; the host only replays the graph and reads the
+// device state back at a few check points, so steps are taken without a
+// host round trip per step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mm.h"
+#include "mm_internal.h"
+
+using namespace mm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define MM_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kGamma = 1.7595e11;
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+struct StateBlobHeader {
+  unsigned magic;
+  int nx, ny, nz;
+  unsigned devstate_size;
+  int k1_valid;
+};
+
+}  // namespace
+
+struct mm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Geom g{};
+  double dx = 0, dy = 0, dz = 0;
+  Buffers b{};
+  // host-side tables
+  mm_material mat[kRegions];
+  std::vector<double> S;        // [256][256]
+  double b0[kRegions][3]{}, b1[kRegions][3]{};
+  double freq = 0, phase = 0;
+  Terms T{1, 1, 1, 1};
+  int precession = 1;
+  bool lut_dirty = true;
+  bool m_set = false;
+  bool k1_valid = false;
+  // graph of one attempt
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+  DevState* st_host = nullptr;   // pinned mirror
+  int fixed_cap = 0;
+  int fixed_n = 0;   // host copy of the replay length
+  long long launches = 0;        // kernels launched (host count)
+  long long graph_nodes = 0;     // kernels per captured attempt
+};
+
+namespace {
+
+int read_state(mm_ctx* c) {
+  MM_CUDA(cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+int write_state(mm_ctx* c) {
+  MM_CUDA(cudaMemcpyAsync(c->b.st, c->st_host, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+// Derived float tables from the float64 host parameters.
+int flush_luts(mm_ctx* c) {
+  if (!c->lut_dirty) return MM_OK;
+  RegionLUT L{};
+  std::vector<float> X((size_t)kRegions * kRegions, 0.0f);
+  double a[kRegions];
+  for (int r = 0; r < kRegions; ++r) {
+    const mm_material& m = c->mat[r];
+    L.msat[r] = (float)m.msat;
+    L.alpha[r] = (float)m.alpha;
+    L.gfac[r] = (float)(-m.gamma_ll / (1.0 + m.alpha * m.alpha));
+    L.k1[r] = m.msat > 0 ? (float)(2.0 * m.ku1 / m.msat) : 0.0f;
+    L.k2[r] = m.msat > 0 ? (float)(4.0 * m.ku2 / m.msat) : 0.0f;
+    double u[3] = {m.anis_u[0], m.anis_u[1], m.anis_u[2]};
+    const double nu = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int k = 0; k < 3; ++k) {
+      L.u[k][r] = nu > 0 ? (float)(u[k] / nu) : 0.0f;
+      L.b0[k][r] = (float)c->b0[r][k];
+      L.b1[k][r] = (float)c->b1[r][k];
+    }
+    a[r] = m.msat > 0 ? m.aex / m.msat : 0.0;
+  }
+  // 2 S(r1, r2) * harmonic mean of Aex/Msat (inter-region exchange)
+  for (int r1 = 0; r1 < kRegions; ++r1)
+    for (int r2 = 0; r2 < kRegions; ++r2) {
+      const double s = a[r1] + a[r2];
+      const double h = s != 0.0 ? 2.0 * a[r1] * a[r2] / s : 0.0;
+      X[(size_t)r1 * kRegions + r2] = (float)(2.0 * c->S[(size_t)r1 * kRegions + r2] * h);
+    }
+  MM_CUDA(cudaMemcpyAsync(c->b.lut, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
+  MM_CUDA(cudaMemcpyAsync(c->b.xlut, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->lut_dirty = false;
+  return MM_OK;
+}
+
+void invalidate(mm_ctx* c) {
+  c->k1_valid = false;
+}
+
+// kernels one demag convolution launches (see launch_demag)
+int demag_launches(const Geom& g) {
+  int mid = g.pz > 1 ? (g.py > 1 ? 3 : 1) : 1;
+  return 2 + mid;
+}
+
+// stage-1 torque at the current m (FSAL start)
+void enqueue_k1(mm_ctx* c) {
+  c->launches += 2 + (c->T.demag ? demag_launches(c->g) : 0);
+  launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
+  if (c->T.demag) launch_demag(c->g, c->b, c->b.ms, c->stream);
+  launch_torque_t(c->g, c->b, c->T, 0, c->freq, c->phase, c->stream);
+}
+
+void enqueue_attempt(mm_ctx* c) {
+  for (int s = 1; s < 7; ++s) {
+    launch_stage_input(c->g, c->b, s, c->stream);
+    if (c->T.demag) launch_demag(c->g, c->b, c->b.ms, c->stream);
+    launch_torque_t(c->g, c->b, c->T, s, c->freq, c->phase, c->stream);
+  }
+  launch_error_control(c->g, c->b, c->stream);
+}
+
+int build_graph(mm_ctx* c) {
+  if (c->graph_valid) return MM_OK;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaGraph_t gr = nullptr;
+  MM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_attempt(c);
+  MM_CUDA(cudaStreamEndCapture(c->stream, &gr));
+  size_t nodes = 0;
+  cudaGraphGetNodes(gr, nullptr, &nodes);
+  c->graph_nodes = (long long)nodes;
+  cudaError_t e = cudaGraphInstantiate(&c->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(MM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->graph_valid = true;
+  return MM_OK;
+}
+
+int status_to_code(int status) {
+  if (status == MM_ERR_NONFINITE) return fail(MM_ERR_NONFINITE, "non-finite step error (NaN/Inf in m or torque)");
+  if (status == MM_ERR_DT_UNDERFLOW) return fail(MM_ERR_DT_UNDERFLOW, "time step fell below dt_min");
+  if (status != 0) return fail(status, "device status error");
+  return MM_OK;
+}
+
+// The stepping loop shared by mm_step and mm_run.  Launches are queued
+// without waiting: the begin kernel, the first-stage evaluation and a first
+// batch of attempts; the device state is read back only at check points.
+int drive(mm_ctx* c, int mode, long long nsteps, double t_end) {
+  if (!c->m_set) return fail(MM_ERR_STATE, "m has not been set");
+  int rc = flush_luts(c);
+  if (rc) return rc;
+  rc = build_graph(c);
+  if (rc) return rc;
+  launch_begin_mode(c->b, mode, nsteps, t_end, c->stream);
+  c->launches += 1;
+  if (!c->k1_valid) enqueue_k1(c);   // no-op on the device if begin found nothing to do
+  MM_CUDA(cudaGetLastError());
+  const bool k1_was_valid = c->k1_valid;
+  // at least one attempt per remaining step; then re-check
+  long long batch = mode == 1 ? 4 : std::max<long long>(1, nsteps);
+  for (int guard = 0; guard < 1000000; ++guard) {
+    batch = std::min<long long>(batch, 4096);
+    for (long long i = 0; i < batch; ++i) MM_CUDA(cudaGraphLaunch(c->graph, c->stream));
+    c->launches += batch * c->graph_nodes;
+    rc = read_state(c);
+    if (rc) return rc;
+    const DevState& s = *c->st_host;
+    // the first-stage torque was evaluated iff an attempt ran in this call
+    c->k1_valid = k1_was_valid || s.call_attempts > 0;
+    if (s.done) return status_to_code(s.status);
+    const long long att = s.accepted + s.rejected;
+    const double rej = att > 0 ? (double)s.rejected / att : 0.0;
+    long long left;
+    if (mode == 1) left = (long long)std::ceil((s.t_end - s.t) / std::max(s.dt, 1e-300)) + 1;
+    else left = s.target - s.accepted;
+    batch = std::max<long long>(1, (long long)std::ceil(left * (1.0 + 2.0 * rej)));
+  }
+  return fail(MM_ERR_STATE, "stepping loop did not finish");
+}
+
+int eval_field(mm_ctx* c, int mode) {
+  int rc = flush_luts(c);
+  if (rc) return rc;
+  rc = read_state(c);
+  if (rc) return rc;
+  Buffers nb = c->b;
+  nb.st = nullptr;    // getters ignore the stepping loop's done flag
+  launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
+  if (c->T.demag || mode == 3) launch_demag(c->g, nb, c->b.ms, c->stream);
+  if (mode == 3) return MM_OK;
+  if (mode == 2) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 8 * sizeof(double), c->stream));
+  Terms T = c->T;
+  launch_field_out_t(c->g, c->b, T, c->b.ms, mode, c->freq, c->phase, c->stream);
+  MM_CUDA(cudaGetLastError());
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mm_last_error(void) { return g_err.c_str(); }
+
+int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double dz, int device, void* stream) {
+  if (!out) return fail(MM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(MM_ERR_ARG, "grid sizes must be >= 1");
+  if (nx > 1024 || ny > 512 || nz > 512)
+    return fail(MM_ERR_ARG, "grid too large: nx <= 1024, ny <= 512, nz <= 512");
+  if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return fail(MM_ERR_ARG, "cell sizes must be > 0");
+  MM_CUDA(cudaSetDevice(device));
+  mm_ctx* c = new mm_ctx();
+  c->device = device;
+  c->dx = dx;
+  c->dy = dy;
+  c->dz = dz;
+  Geom& g = c->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.n = (long long)nx * ny * nz;
+  g.idx2 = (float)(1.0 / (dx * dx));
+  g.idy2 = (float)(1.0 / (dy * dy));
+  g.idz2 = (float)(1.0 / (dz * dz));
+  g.px = nx == 1 ? 1 : next_pow2(2 * nx - 1);
+  g.py = ny == 1 ? 1 : next_pow2(2 * ny - 1);
+  g.pz = nz == 1 ? 1 : next_pow2(2 * nz - 1);
+  g.lx = g.px == 1 ? 1 : g.px / 2;
+  g.hx = g.px == 1 ? 1 : g.lx + 1;
+  g.hxs = (g.hx + 7) / 8 * 8;
+  g.srows = g.pz > 1 ? g.py : ny;
+  g.sc = (long long)nz * g.srows * g.hxs;
+  g.hkx = g.px == 1 ? 1 : g.px / 2 + 1;
+  g.hky = g.py == 1 ? 1 : g.py / 2 + 1;
+  g.hkz = g.pz == 1 ? 1 : g.pz / 2 + 1;
+  for (int r = 0; r < kRegions; ++r) {
+    std::memset(&c->mat[r], 0, sizeof(mm_material));
+    c->mat[r].gamma_ll = kGamma;
+    c->mat[r].anis_u[0] = 1.0;
+  }
+  c->S.assign((size_t)kRegions * kRegions, 1.0);
+
+  auto cleanup = [&](int code) {
+    mm_destroy(c);
+    return code;
+  };
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, cudaGetErrorString(e)));
+    c->own_stream = true;
+  }
+  const size_t vec = 3 * (size_t)g.n * sizeof(float);
+  Buffers& b = c->b;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, c->stream);
+  };
+  alloc((void**)&b.m[0], vec);
+  alloc((void**)&b.m[1], vec);
+  for (int j = 0; j < 7; ++j) alloc((void**)&b.k[j], vec);
+  alloc((void**)&b.ms, vec);
+  alloc((void**)&b.bd, vec);
+  alloc((void**)&b.out, vec);
+  alloc((void**)&b.spec, 3 * (size_t)g.sc * sizeof(float2));
+  alloc((void**)&b.kt, 6 * (size_t)g.hkx * g.hky * g.hkz * sizeof(float));
+  alloc((void**)&b.tw, 2048 * sizeof(float2));
+  alloc((void**)&b.mask, (size_t)g.n);
+  alloc((void**)&b.region, (size_t)g.n);
+  alloc((void**)&b.lut, sizeof(RegionLUT));
+  alloc((void**)&b.xlut, (size_t)kRegions * kRegions * sizeof(float));
+  alloc((void**)&b.st, devstate_bytes());
+  alloc((void**)&b.hist, (size_t)kHistCap * sizeof(double));
+  alloc((void**)&b.acc, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->st_host, sizeof(DevState));
+  if (e != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, cudaGetErrorString(e)));
+  // twiddles
+  std::vector<float2> tw(2048);
+  for (int k = 0; k < 2048; ++k) {
+    const double a = -2.0 * kPi * k / 2048.0;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  e = cudaMemcpyAsync(b.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  std::vector<uint8_t> ones((size_t)g.n, 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.mask, ones.data(), ones.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, cudaGetErrorString(e)));
+  // demag kernel (float64 on the device)
+  e = build_kernel_spectrum(g, dx, dy, dz, b.kt, c->stream);
+  if (e != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,
+                        std::string("kernel precompute: ") + cudaGetErrorString(e)));
+  // device state defaults (Sec. IV: MaxErr 1e-5, headroom 0.8)
+  DevState& s = *c->st_host;
+  std::memset(&s, 0, sizeof(DevState));
+  s.dt = 1e-14;
+  s.max_err = 1e-5;
+  s.headroom = 0.8;
+  s.dt_min = 1e-20;
+  s.dt_max = 1e-10;
+  s.precession = 1;
+  s.done = 1;
+  int rc = write_state(c);
+  if (rc) return cleanup(rc);
+  rc = flush_luts(c);
+  if (rc) return cleanup(rc);
+  // one convolution outside any capture: sets per-kernel launch attributes
+  Buffers nb = b;
+  nb.st = nullptr;
+  launch_demag(g, nb, b.ms, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, std::string("warm-up: ") + cudaGetErrorString(e)));
+  *out = c;
+  return MM_OK;
+}
+
+int mm_destroy(mm_ctx* c) {
+  if (!c) return MM_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  Buffers& b = c->b;
+  void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.bd, b.out,
+                  b.spec, b.kt, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return MM_OK;
+}
+
+int mm_set_geometry(mm_ctx* c, const uint8_t* mask) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  std::vector<uint8_t> v((size_t)c->g.n, 1);
+  if (mask)
+    for (long long i = 0; i < c->g.n; ++i) v[i] = mask[i] ? 1 : 0;
+  MM_CUDA(cudaMemcpyAsync(c->b.mask, v.data(), v.size(), cudaMemcpyHostToDevice, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_set_regions(mm_ctx* c, const uint8_t* region) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  std::vector<uint8_t> v((size_t)c->g.n, 0);
+  if (region) std::memcpy(v.data(), region, v.size());
+  MM_CUDA(cudaMemcpyAsync(c->b.region, v.data(), v.size(), cudaMemcpyHostToDevice, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_set_region_material(mm_ctx* c, int region, const mm_material* mat) {
+  if (!c || !mat) return fail(MM_ERR_ARG, "NULL argument");
+  if (region < 0 || region >= kRegions) return fail(MM_ERR_ARG, "region must be 0..255");
+  if (mat->msat < 0 || mat->aex < 0 || mat->alpha < 0 || !std::isfinite(mat->gamma_ll))
+    return fail(MM_ERR_ARG, "msat, aex, alpha must be >= 0");
+  c->mat[region] = *mat;
+  c->lut_dirty = true;
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_set_exchange_scale(mm_ctx* c, int r1, int r2, double S) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (r1 < 0 || r1 >= kRegions || r2 < 0 || r2 >= kRegions) return fail(MM_ERR_ARG, "region must be 0..255");
+  c->S[(size_t)r1 * kRegions + r2] = S;
+  c->S[(size_t)r2 * kRegions + r1] = S;
+  c->lut_dirty = true;
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_set_bext(mm_ctx* c, int region, const double b0[3], const double b1[3]) {
+  if (!c || !b0) return fail(MM_ERR_ARG, "NULL argument");
+  if (region < -1 || region >= kRegions) return fail(MM_ERR_ARG, "region must be -1..255");
+  const int lo = region < 0 ? 0 : region, hi = region < 0 ? kRegions : region + 1;
+  for (int r = lo; r < hi; ++r)
+    for (int k = 0; k < 3; ++k) {
+      c->b0[r][k] = b0[k];
+      c->b1[r][k] = b1 ? b1[k] : 0.0;
+    }
+  c->lut_dirty = true;
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_set_bext_timefn(mm_ctx* c, double freq, double phase) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  c->freq = freq;
+  c->phase = phase;
+  c->graph_valid = false;
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_enable_terms(mm_ctx* c, int demag, int exch, int anis, int zeeman, int precession) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  c->T = Terms{demag != 0, exch != 0, anis != 0, zeeman != 0};
+  int rc = read_state(c);
+  if (rc) return rc;
+  c->st_host->precession = precession != 0;
+  rc = write_state(c);
+  if (rc) return rc;
+  c->graph_valid = false;
+  invalidate(c);
+  return MM_OK;
+}
+
+static int set_m_common(mm_ctx* c, const float* src, cudaMemcpyKind kind) {
+  int rc = flush_luts(c);
+  if (rc) return rc;
+  rc = read_state(c);
+  if (rc) return rc;
+  float* dst = c->b.m[c->st_host->parity];
+  MM_CUDA(cudaMemcpyAsync(dst, src, 3 * (size_t)c->g.n * sizeof(float), kind, c->stream));
+  launch_normalize(c->g, c->b, dst, c->stream);
+  MM_CUDA(cudaGetLastError());
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->m_set = true;
+  invalidate(c);
+  return MM_OK;
+}
+
+int mm_set_m(mm_ctx* c, const float* m) {
+  if (!c || !m) return fail(MM_ERR_ARG, "NULL argument");
+  return set_m_common(c, m, cudaMemcpyHostToDevice);
+}
+
+int mm_set_m_device(mm_ctx* c, const float* m) {
+  if (!c || !m) return fail(MM_ERR_ARG, "NULL argument");
+  return set_m_common(c, m, cudaMemcpyDeviceToDevice);
+}
+
+static int get_m_common(mm_ctx* c, float* dst, cudaMemcpyKind kind) {
+  int rc = read_state(c);
+  if (rc) return rc;
+  MM_CUDA(cudaMemcpyAsync(dst, c->b.m[c->st_host->parity], 3 * (size_t)c->g.n * sizeof(float), kind, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+int mm_get_m(mm_ctx* c, float* m) {
+  if (!c || !m) return fail(MM_ERR_ARG, "NULL argument");
+  return get_m_common(c, m, cudaMemcpyDeviceToHost);
+}
+
+int mm_get_m_device(mm_ctx* c, float* m) {
+  if (!c || !m) return fail(MM_ERR_ARG, "NULL argument");
+  return get_m_common(c, m, cudaMemcpyDeviceToDevice);
+}
+
+int mm_set_solver(mm_ctx* c, double max_err, double headroom, double dt0, double dt_min, double dt_max) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (!(max_err > 0) || !(headroom > 0) || !(dt0 > 0) || !(dt_min > 0) || !(dt_max >= dt_min))
+    return fail(MM_ERR_ARG, "solver settings must be positive with dt_min <= dt_max");
+  int rc = read_state(c);
+  if (rc) return rc;
+  DevState& s = *c->st_host;
+  s.max_err = max_err;
+  s.headroom = headroom;
+  s.dt = std::min(std::max(dt0, dt_min), dt_max);
+  s.dt_min = dt_min;
+  s.dt_max = dt_max;
+  return write_state(c);
+}
+
+int mm_set_fixed_dt_sequence(mm_ctx* c, const double* dts, int n) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && !dts)) return fail(MM_ERR_ARG, "bad sequence");
+  for (int i = 0; i < n; ++i)
+    if (!(dts[i] > 0) || !std::isfinite(dts[i])) return fail(MM_ERR_ARG, "step sizes must be finite and > 0");
+  if (n > c->fixed_cap) {
+    if (c->b.fixed) cudaFree(c->b.fixed);
+    c->b.fixed = nullptr;
+    c->fixed_cap = 0;
+    MM_CUDA(cudaMalloc((void**)&c->b.fixed, (size_t)n * sizeof(double)));
+    c->fixed_cap = n;
+    c->graph_valid = false;   // the error kernel's pointer changed
+  }
+  if (n > 0)
+    MM_CUDA(cudaMemcpyAsync(c->b.fixed, dts, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  int rc = read_state(c);
+  if (rc) return rc;
+  c->st_host->fixed_idx = 0;
+  c->st_host->fixed_n = n;
+  c->fixed_n = n;
+  return write_state(c);
+}
+
+int mm_step(mm_ctx* c, int n) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (n < 0) return fail(MM_ERR_ARG, "n must be >= 0");
+  if (n == 0) return MM_OK;
+  const int mode = c->fixed_n > 0 ? 2 : 0;
+  return drive(c, mode, n, 0.0);
+}
+
+int mm_run(mm_ctx* c, double t_end) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (!std::isfinite(t_end)) return fail(MM_ERR_ARG, "t_end must be finite");
+  if (c->fixed_n > 0) return fail(MM_ERR_STATE, "run() is not available in replay mode");
+  return drive(c, 1, 0, t_end);
+}
+
+int mm_get_time(mm_ctx* c, double* t, double* dt) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  int rc = read_state(c);
+  if (rc) return rc;
+  if (t) *t = c->st_host->t;
+  if (dt) *dt = c->st_host->dt;
+  return MM_OK;
+}
+
+int mm_set_time(mm_ctx* c, double t, double dt) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (!std::isfinite(t) || !(dt > 0)) return fail(MM_ERR_ARG, "bad time or step");
+  int rc = read_state(c);
+  if (rc) return rc;
+  c->st_host->t = t;
+  c->st_host->dt = dt;
+  invalidate(c);
+  return write_state(c);
+}
+
+static int copy_out(mm_ctx* c, const float* src, float* dst) {
+  MM_CUDA(cudaMemcpyAsync(dst, src, 3 * (size_t)c->g.n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+int mm_get_beff(mm_ctx* c, float* b) {
+  if (!c || !b) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = eval_field(c, 0);
+  return rc ? rc : copy_out(c, c->b.out, b);
+}
+
+int mm_get_torque(mm_ctx* c, float* tau) {
+  if (!c || !tau) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = eval_field(c, 1);
+  return rc ? rc : copy_out(c, c->b.out, tau);
+}
+
+int mm_get_bdemag(mm_ctx* c, float* b) {
+  if (!c || !b) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = eval_field(c, 3);
+  return rc ? rc : copy_out(c, c->b.bd, b);
+}
+
+int mm_get_energies(mm_ctx* c, mm_energies* out) {
+  if (!c || !out) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = eval_field(c, 2);
+  if (rc) return rc;
+  double acc[8];
+  MM_CUDA(cudaMemcpyAsync(acc, c->b.acc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  const double V = c->dx * c->dy * c->dz;
+  out->demag = acc[0] * V;
+  out->exch = acc[1] * V;
+  out->anis = acc[2] * V;
+  out->zeeman = acc[3] * V;
+  out->total = out->demag + out->exch + out->anis + out->zeeman;
+  for (int k = 0; k < 3; ++k) out->m_avg[k] = acc[7] > 0 ? acc[4 + k] / acc[7] : 0.0;
+  return MM_OK;
+}
+
+int mm_get_stats(mm_ctx* c, mm_stats* s) {
+  if (!c || !s) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = read_state(c);
+  if (rc) return rc;
+  const DevState& d = *c->st_host;
+  s->accepted = d.accepted;
+  s->rejected = d.rejected;
+  s->evals = d.evals;
+  s->last_err = d.last_err;
+  s->t = d.t;
+  s->dt = d.dt;
+  s->launches = c->launches;
+  return MM_OK;
+}
+
+int mm_get_dt_history(mm_ctx* c, double* dts, int max, int* n) {
+  if (!c || !n || (max > 0 && !dts)) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = read_state(c);
+  if (rc) return rc;
+  const int avail = std::min(c->st_host->hist_n, kHistCap);
+  const int k = std::min(avail, std::max(max, 0));
+  if (k > 0) {
+    MM_CUDA(cudaMemcpyAsync(dts, c->b.hist, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  *n = k;
+  return MM_OK;
+}
+
+size_t mm_state_bytes(mm_ctx* c) {
+  if (!c) return 0;
+  return sizeof(StateBlobHeader) + sizeof(DevState) + 4 * 3 * (size_t)c->g.n * sizeof(float);
+}
+
+int mm_get_state(mm_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf) return fail(MM_ERR_ARG, "NULL argument");
+  if (bytes < mm_state_bytes(c)) return fail(MM_ERR_ARG, "buffer too small");
+  int rc = read_state(c);
+  if (rc) return rc;
+  char* p = (char*)buf;
+  StateBlobHeader h{0x6d6d3435u, c->g.nx, c->g.ny, c->g.nz, (unsigned)sizeof(DevState), c->k1_valid ? 1 : 0};
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  std::memcpy(p, c->st_host, sizeof(DevState));
+  p += sizeof(DevState);
+  const size_t vb = 3 * (size_t)c->g.n * sizeof(float);
+  float* src[4] = {c->b.m[0], c->b.m[1], c->b.k[0], c->b.k[6]};
+  for (float* s : src) {
+    MM_CUDA(cudaMemcpyAsync(p, s, vb, cudaMemcpyDeviceToHost, c->stream));
+    p += vb;
+  }
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+int mm_set_state(mm_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return fail(MM_ERR_ARG, "NULL argument");
+  if (bytes < mm_state_bytes(c)) return fail(MM_ERR_ARG, "buffer too small");
+  const char* p = (const char*)buf;
+  StateBlobHeader h;
+  std::memcpy(&h, p, sizeof(h));
+  if (h.magic != 0x6d6d3435u || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz ||
+      h.devstate_size != sizeof(DevState))
+    return fail(MM_ERR_ARG, "state blob does not match this context");
+  p += sizeof(h);
+  DevState s;
+  std::memcpy(&s, p, sizeof(DevState));
+  p += sizeof(DevState);
+  s.done = 1;
+  s.ticket = 0;
+  s.err_bits = 0;
+  s.fixed_idx = s.fixed_n = 0;   // the replay sequence is not part of a checkpoint
+  c->fixed_n = 0;
+  *c->st_host = s;
+  int rc = write_state(c);
+  if (rc) return rc;
+  const size_t vb = 3 * (size_t)c->g.n * sizeof(float);
+  float* dst[4] = {c->b.m[0], c->b.m[1], c->b.k[0], c->b.k[6]};
+  for (float* d : dst) {
+    MM_CUDA(cudaMemcpyAsync(d, p, vb, cudaMemcpyHostToDevice, c->stream));
+    p += vb;
+  }
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->m_set = true;
+  c->k1_valid = h.k1_valid != 0;
+  return MM_OK;
+}
+
+int mm_demag_tensor(int device, double dx, double dy, double dz, int n, const int32_t* offsets, double* out) {
+  if (n < 0 || (n > 0 && (!offsets || !out))) return fail(MM_ERR_ARG, "bad arguments");
+  if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return fail(MM_ERR_ARG, "cell sizes must be > 0");
+  if (n == 0) return MM_OK;
+  MM_CUDA(cudaSetDevice(device));
+  int32_t* d_off = nullptr;
+  double* d_out = nullptr;
+  cudaError_t e = cudaMalloc(&d_off, (size_t)n * 3 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)n * 6 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d_off, offsets, (size_t)n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = demag_tensor_offsets(n, d_off, dx, dy, dz, d_out, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, (size_t)n * 6 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_off);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(MM_ERR_CUDA, cudaGetErrorString(e));
+  return MM_OK;
+}
+
+int mm_demag_apply(mm_ctx* c, const float* m, float* b) {
+  if (!c || !m || !b) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = flush_luts(c);
+  if (rc) return rc;
+  Buffers nb = c->b;
+  nb.st = nullptr;
+  nb.bd = b;
+  launch_demag(c->g, nb, m, c->stream);
+  MM_CUDA(cudaGetLastError());
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+int mm_sync(mm_ctx* c) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mm {
+
+constexpr int kRegions = 256;
+constexpr int kHistCap = 1 << 20;   // accepted-step sizes kept for replay
+
+// Per-region parameters, float32, derived on the host from mm_material
+// (Sec. II.A: 256-entry look-up tables indexed by the region byte).
+struct RegionLUT {
+  float msat[kRegions];
+  float alpha[kRegions];
+  float gfac[kRegions];   // -gamma / (1 + alpha^2)   (Eq. eqLLG, damping sign)
+  float k1[kRegions];     // 2 Ku1 / Msat            (uniaxial field, Ku1 part)
+  float k2[kRegions];     // 4 Ku2 / Msat            (uniaxial field, Ku2 part)
+  float u[3][kRegions];   // anisotropy axis
+  float b0[3][kRegions];  // B_ext = b0 + b1 sin(2 pi f t + phase)
+  float b1[3][kRegions];
+};
+
+// Grid and padded-FFT geometry.
+struct Geom {
+  int nx, ny, nz;
+  long long n;            // nx * ny * nz
+  float idx2, idy2, idz2; // 1 / d^2 per axis
+  int px, py, pz;         // padded sizes (power of two >= 2n - 1; 1 if n == 1)
+  int lx;                 // complex length of the x transform (px / 2, or 1)
+  int hx;                 // spectrum columns kept along x: lx + 1 (or 1)
+  int hxs;                // row stride of the spectrum buffer (complex)
+  int srows;              // rows per plane in the spectrum buffer (py if pz > 1 else ny)
+  long long sc;           // complex elements per component of the spectrum buffer
+  int hkx, hky, hkz;      // octant sizes of the kernel spectrum
+};
+
+// Integrator state on the device (one per context).  Every kernel of a step
+// reads it, so a captured graph of one attempt can be replayed unchanged.
+struct DevState {
+  double t, dt, h;          // time, proposed step, step of the current attempt
+  double t_end;             // run() target
+  double max_err, headroom, dt_min, dt_max;
+  double last_err;
+  double stage_t[7];        // t + c_s h
+  long long accepted, rejected, evals;
+  long long target;         // steps(): stop at this accepted count
+  int mode;                 // 0 steps(n), 1 run(t_end), 2 replay
+  int parity;               // which m / k1 buffers are current (FSAL swap)
+  int done;                 // 1: no more attempts in this call
+  int status;               // MM_OK or an error code
+  int fixed_idx, fixed_n;   // replay cursor
+  int hist_n;
+  unsigned int err_bits;    // max step error of this attempt (float bits)
+  unsigned int ticket;      // last-block election in the error kernel
+  int call_attempts;         // attempts since the last begin
+  int precession;
+};
+
+struct Buffers {
+  float* m[2];        // current / candidate m (parity)
+  float* k[7];        // RK stages; k[0] and k[6] swap roles with parity
+  float* ms;          // stage input m_s
+  float* bd;          // demag field
+  float2* spec;       // spectrum work buffer
+  float* kt;          // kernel spectrum octant [6][hkz][hky][hkx]
+  float2* tw;         // twiddles W[k] = exp(-2 pi i k / 2048)
+  uint8_t* mask;
+  uint8_t* region;
+  RegionLUT* lut;
+  float* xlut;        // [256][256]: 2 S H(Aex/Msat) exchange couplings
+  DevState* st;
+  double* hist;       // accepted step sizes
+  double* fixed;      // replay sequence
+  double* acc;        // energy accumulators
+  float* out;         // field/torque output for getters
+};
+
+struct Terms { int demag, exch, anis, zeeman; };
+
+// ---- launch wrappers (stream-ordered) ----
+// demag convolution of M = Msat m (m = `m`), result in b.bd
+void launch_demag(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
+// kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
+cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
+                                  cudaStream_t s);
+cudaError_t demag_tensor_offsets(int n, const int32_t* d_off, double dx, double dy, double dz,
+                                 double* d_out, cudaStream_t s);
+
+// RK45 pieces (llg.cu).  DevState is followed in the same allocation by the
+// per-attempt stage coefficients; devstate_bytes() is the allocation size.
+size_t devstate_bytes();
+// mode 0: steps(nsteps); 1: run(t_end); 2: replay of the fixed sequence
+void launch_begin_mode(const Buffers& b, int mode, long long nsteps, double t_end, cudaStream_t s);
+void launch_stage_input(const Geom& g, const Buffers& b, int stage, cudaStream_t s);
+// torque of stage `stage` (0..6) at m_s (stage 0: the current m), into the
+// k buffer holding that stage's role
+void launch_torque_t(const Geom& g, const Buffers& b, const Terms& T, int stage, double freq, double phase,
+                     cudaStream_t s);
+void launch_error_control(const Geom& g, const Buffers& b, cudaStream_t s);
+void launch_copy_mcur(const Geom& g, const Buffers& b, float* dst, cudaStream_t s);
+// getters at m, time st->t: mode 0 B_eff -> b.out, 1 torque -> b.out,
+// 2 energy sums -> b.acc
+void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const float* m, int mode, double freq,
+                        double phase, cudaStream_t s);
+void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s);
+
+}  // namespace mm

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the C ABI in include/mm.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libmm.so``; if it is
+missing this module raises at import time -- there is no CPU fallback.
+Module-level functions carry the ABI's names; ``Context`` wraps a handle and
+``Context.from_problem`` configures one from a ``workloads.Problem``.
+Arrays cross the boundary as float32 SoA (3, nz, ny, nx) and uint8 maps
+(nz, ny, nx); device variants take torch CUDA tensors (memory only).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"CUDA library not built ({LIB}); run paper_1406_7635_gb300.build.build()")
+
+_lib = C.CDLL(LIB)
+
+MM_OK = 0
+ERRORS = {-1: "MM_ERR_ARG", -2: "MM_ERR_CUDA", -3: "MM_ERR_OOM", -4: "MM_ERR_NONFINITE",
+          -5: "MM_ERR_DT_UNDERFLOW", -6: "MM_ERR_TIMEOUT", -7: "MM_ERR_STATE"}
+
+
+class MMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mm_material(C.Structure):
+    _fields_ = [("msat", C.c_double), ("aex", C.c_double), ("alpha", C.c_double), ("gamma_ll", C.c_double),
+                ("ku1", C.c_double), ("ku2", C.c_double), ("anis_u", C.c_double * 3)]
+
+
+class mm_energies(C.Structure):
+    _fields_ = [("total", C.c_double), ("demag", C.c_double), ("exch", C.c_double), ("anis", C.c_double),
+                ("zeeman", C.c_double), ("m_avg", C.c_double * 3)]
+
+
+class mm_stats(C.Structure):
+    _fields_ = [("accepted", C.c_longlong), ("rejected", C.c_longlong), ("evals", C.c_longlong),
+                ("last_err", C.c_double), ("t", C.c_double), ("dt", C.c_double), ("launches", C.c_longlong)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_SIGS = {
+    "mm_last_error": (C.c_char_p, []),
+    "mm_create": (_I, [C.POINTER(_P), _I, _I, _I, _D, _D, _D, _I, _P]),
+    "mm_destroy": (_I, [_P]),
+    "mm_set_geometry": (_I, [_P, _P]),
+    "mm_set_regions": (_I, [_P, _P]),
+    "mm_set_region_material": (_I, [_P, _I, C.POINTER(mm_material)]),
+    "mm_set_exchange_scale": (_I, [_P, _I, _I, _D]),
+    "mm_set_bext": (_I, [_P, _I, _P, _P]),
+    "mm_set_bext_timefn": (_I, [_P, _D, _D]),
+    "mm_enable_terms": (_I, [_P, _I, _I, _I, _I, _I]),
+    "mm_set_m": (_I, [_P, _P]),
+    "mm_get_m": (_I, [_P, _P]),
+    "mm_set_m_device": (_I, [_P, _P]),
+    "mm_get_m_device": (_I, [_P, _P]),
+    "mm_set_solver": (_I, [_P, _D, _D, _D, _D, _D]),
+    "mm_set_fixed_dt_sequence": (_I, [_P, _P, _I]),
+    "mm_step": (_I, [_P, _I]),
+    "mm_run": (_I, [_P, _D]),
+    "mm_get_time": (_I, [_P, C.POINTER(_D), C.POINTER(_D)]),
+    "mm_set_time": (_I, [_P, _D, _D]),
+    "mm_get_beff": (_I, [_P, _P]),
+    "mm_get_bdemag": (_I, [_P, _P]),
+    "mm_get_torque": (_I, [_P, _P]),
+    "mm_get_energies": (_I, [_P, C.POINTER(mm_energies)]),
+    "mm_get_stats": (_I, [_P, C.POINTER(mm_stats)]),
+    "mm_get_dt_history": (_I, [_P, _P, _I, C.POINTER(_I)]),
+    "mm_state_bytes": (C.c_size_t, [_P]),
+    "mm_get_state": (_I, [_P, _P, C.c_size_t]),
+    "mm_set_state": (_I, [_P, _P, C.c_size_t]),
+    "mm_demag_tensor": (_I, [_I, _D, _D, _D, _I, _P, _P]),
+    "mm_demag_apply": (_I, [_P, _P, _P]),
+    "mm_sync": (_I, [_P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+EXPORTED = sorted(_SIGS)
+
+
+def _check(rc):
+    if rc != MM_OK:
+        raise MMError(rc, mm_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def demag_tensor(offsets, dx, dy, dz, device=0):
+    """N_ij (float64, [n, 6]) for integer offsets [n, 3] computed on the GPU."""
+    off = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((off.shape[0], 6), dtype=np.float64)
+    _check(mm_demag_tensor(device, dx, dy, dz, off.shape[0], _ptr(off), _ptr(out)))
+    return out
+
+
+class Context:
+    """A grid, its materials and its integrator state on one GPU."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, device=0, stream=None):
+        h = C.c_void_p()
+        _check(mm_create(C.byref(h), nx, ny, nz, dx, dy, dz, device, stream))
+        self.h = h
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+
+    def close(self):
+        if self.h:
+            mm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- set-up ---
+    def set_geometry(self, mask):
+        a = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(self.shape)
+        _check(mm_set_geometry(self.h, None if a is None else _ptr(a)))
+
+    def set_regions(self, region):
+        a = None if region is None else np.ascontiguousarray(region, dtype=np.uint8).reshape(self.shape)
+        _check(mm_set_regions(self.h, None if a is None else _ptr(a)))
+
+    def set_material(self, region, msat, aex, alpha, gamma_ll=1.7595e11, ku1=0.0, ku2=0.0, anis_u=(1.0, 0.0, 0.0)):
+        m = mm_material(msat, aex, alpha, gamma_ll, ku1, ku2, (C.c_double * 3)(*anis_u))
+        _check(mm_set_region_material(self.h, region, C.byref(m)))
+
+    def set_exchange_scale(self, r1, r2, s):
+        _check(mm_set_exchange_scale(self.h, r1, r2, s))
+
+    def set_bext(self, region, b0, b1=None):
+        a0 = np.ascontiguousarray(b0, dtype=np.float64)
+        a1 = None if b1 is None else np.ascontiguousarray(b1, dtype=np.float64)
+        _check(mm_set_bext(self.h, region, _ptr(a0), None if a1 is None else _ptr(a1)))
+
+    def set_bext_timefn(self, freq, phase=0.0):
+        _check(mm_set_bext_timefn(self.h, freq, phase))
+
+    def enable_terms(self, demag=True, exch=True, anis=True, zeeman=True, precession=True):
+        _check(mm_enable_terms(self.h, int(demag), int(exch), int(anis), int(zeeman), int(precession)))
+
+    def set_solver(self, max_err=1e-5, headroom=0.8, dt0=1e-14, dt_min=1e-20, dt_max=1e-10):
+        _check(mm_set_solver(self.h, max_err, headroom, dt0, dt_min, dt_max))
+
+    def set_fixed_dt_sequence(self, dts):
+        a = np.ascontiguousarray(dts, dtype=np.float64)
+        _check(mm_set_fixed_dt_sequence(self.h, _ptr(a) if a.size else None, a.size))
+
+    # --- state ---
+    def set_m(self, m):
+        a = np.ascontiguousarray(m, dtype=np.float32).reshape((3,) + self.shape)
+        _check(mm_set_m(self.h, _ptr(a)))
+
+    def get_m(self):
+        out = np.zeros((3,) + self.shape, dtype=np.float32)
+        _check(mm_get_m(self.h, _ptr(out)))
+        return out
+
+    def set_m_device(self, t):
+        assert t.is_cuda and t.dtype.itemsize == 4 and t.is_contiguous() and t.numel() == 3 * self.n
+        _check(mm_set_m_device(self.h, C.c_void_p(t.data_ptr())))
+
+    def get_m_device(self, t):
+        assert t.is_cuda and t.dtype.itemsize == 4 and t.is_contiguous() and t.numel() == 3 * self.n
+        _check(mm_get_m_device(self.h, C.c_void_p(t.data_ptr())))
+
+    def step(self, n):
+        _check(mm_step(self.h, int(n)))
+
+    def run(self, t_end):
+        _check(mm_run(self.h, float(t_end)))
+
+    def get_time(self):
+        t, dt = C.c_double(), C.c_double()
+        _check(mm_get_time(self.h, C.byref(t), C.byref(dt)))
+        return t.value, dt.value
+
+    def set_time(self, t, dt):
+        _check(mm_set_time(self.h, t, dt))
+
+    def _vec(self, fn):
+        out = np.zeros((3,) + self.shape, dtype=np.float32)
+        _check(fn(self.h, _ptr(out)))
+        return out
+
+    def get_beff(self):
+        return self._vec(mm_get_beff)
+
+    def get_bdemag(self):
+        return self._vec(mm_get_bdemag)
+
+    def get_torque(self):
+        return self._vec(mm_get_torque)
+
+    def get_energies(self):
+        e = mm_energies()
+        _check(mm_get_energies(self.h, C.byref(e)))
+        return {"total": e.total, "demag": e.demag, "exch": e.exch, "anis": e.anis, "zeeman": e.zeeman,
+                "m_avg": list(e.m_avg)}
+
+    def get_stats(self):
+        s = mm_stats()
+        _check(mm_get_stats(self.h, C.byref(s)))
+        return {"accepted": s.accepted, "rejected": s.rejected, "evals": s.evals, "last_err": s.last_err,
+                "t": s.t, "dt": s.dt, "launches": s.launches}
+
+    def get_dt_history(self, max_n=1 << 20):
+        out = np.zeros(max_n, dtype=np.float64)
+        n = C.c_int()
+        _check(mm_get_dt_history(self.h, _ptr(out), max_n, C.byref(n)))
+        return out[:n.value].copy()
+
+    def get_state(self):
+        nb = mm_state_bytes(self.h)
+        buf = np.zeros(nb, dtype=np.uint8)
+        _check(mm_get_state(self.h, _ptr(buf), nb))
+        return buf
+
+    def set_state(self, buf):
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(mm_set_state(self.h, _ptr(b), b.size))
+
+    def demag_apply(self, m_dev, b_dev):
+        """B_demag of the device tensor m_dev into b_dev (torch CUDA, float32)."""
+        _check(mm_demag_apply(self.h, C.c_void_p(m_dev.data_ptr()), C.c_void_p(b_dev.data_ptr())))
+
+    def sync(self):
+        _check(mm_sync(self.h))
+
+    # --- configuration from a Problem description ---
+    @classmethod
+    def from_problem(cls, p, device=0, stream=None, regions_used=None):
+        ctx = cls(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, device, stream)
+        ctx.set_geometry(p.mask)
+        ctx.set_regions(p.region)
+        used = np.unique(p.region) if regions_used is None else regions_used
+        for r in used:
+            r = int(r)
+            ctx.set_material(r, p.msat[r], p.aex[r], p.alpha[r], p.gamma[r], p.ku1[r], p.ku2[r], p.anis_u[r])
+            ctx.set_bext(r, p.b0[r], p.b1[r])
+        for i, r1 in enumerate(used):
+            for r2 in used[i + 1:]:
+                s = p.exch_scale[int(r1), int(r2)]
+                if s != 1.0:
+                    ctx.set_exchange_scale(int(r1), int(r2), s)
+        ctx.set_bext_timefn(p.freq, p.phase)
+        ctx.enable_terms(p.demag, p.exch, p.anis, p.zeeman, p.precession)
+        ctx.set_solver(p.max_err, p.headroom, p.dt0, p.dt_min, p.dt_max)
+        ctx.set_m(p.m0)
+        return ctx
