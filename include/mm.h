@@ -168,6 +168,29 @@ int mm_demag_tensor(int device, double dx, double dy, double dz, int n,
  * Ordered on the context's stream; returns after the stream has finished. */
 int mm_demag_apply(mm_ctx* ctx, const float* m, float* b);
 
+/* Demagnetising field B (T) of a magnetisation M = Msat m (A/m) on an
+ * nx*ny*nz grid of dx*dy*dz cells, without allocating device memory.  For
+ * callers that cannot call cudaMalloc: frameworks whose device memory must all
+ * come from their own pool, applications that forbid device allocation after
+ * start-up, real-time loops that must not touch the allocator.  The paper has
+ * no counterpart; the arithmetic is the convolution of mm_demag_apply with a
+ * kernel computed as in mm_create, redone on every call (a context is faster
+ * for repeated use on one grid).
+ *  - M, B: device pointers on the current device, float32 SoA [3][nz][ny][nx];
+ *    the caller owns them.  stream: a cudaStream_t, or NULL.
+ *  - Scratch: one static device array of 32 MiB per GPU that loads the
+ *    library, held until the process exits.  Grids whose kernel precompute,
+ *    kernel spectrum and FFT spectrum do not fit (about 2.4 M padded points in
+ *    2-D, fewer in 3-D) are rejected with MM_ERR_ARG and a message giving the
+ *    bytes needed.  The first call on a device looks up the array's device
+ *    address (cudaGetSymbolAddress); make that first call before capturing
+ *    any stream on that device.
+ *  - Every call uses the same array and leaves its contents behind; calls
+ *    that overlap on the GPU (other streams, other threads) race.  The call
+ *    returns after the stream has finished.  Calls no cudaMalloc/cudaFree. */
+int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
+                           const float* M, float* B, void* stream);
+
 /* Blocks until the context's stream is idle. */
 int mm_sync(mm_ctx* ctx);
 

@@ -234,6 +234,18 @@ void axis_tables(int n, int P, int h, std::vector<double>& tc, std::vector<doubl
     }
 }
 
+// Device-side version of axis_tables (float64 cospi/sinpi of the exactly
+// reduced angle), for callers that must not stage tables from the host.
+__global__ void k_axis_tables(int n, int P, int h, double* __restrict__ tc, double* __restrict__ ts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * h) return;
+  const int k = i / n, X = i % n;
+  const long long num = (2LL * k * X) % (2LL * P);   // angle = pi * num / P
+  const double a = (double)num / (double)P;
+  tc[i] = (X == 0 ? 1.0 : 2.0) * cospi(a);
+  ts[i] = 2.0 * sinpi(a);
+}
+
 }  // namespace
 
 cudaError_t demag_tensor_offsets(int n, const int32_t* d_off, double dx, double dy, double dz,
@@ -294,6 +306,45 @@ cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz
   cudaFree(w1);
   cudaFree(tab);
   return e;
+}
+
+// Same computation as build_kernel_spectrum, on caller-provided work space
+// and without host round trips: w0, w1 hold 6 * kernel_work_doubles(g)
+// doubles each, tab holds 2 * max(n) * max(h) doubles.
+size_t kernel_work_doubles(const Geom& g) {
+  const long long n = g.n;
+  return 6ULL * std::max<long long>(std::max<long long>(n, (long long)g.hkx * g.ny * g.nz),
+                                    std::max<long long>((long long)g.hkx * g.hky * g.nz,
+                                                        (long long)g.hkx * g.hky * g.hkz));
+}
+size_t kernel_table_doubles(const Geom& g) {
+  const int maxn = std::max(g.nx, std::max(g.ny, g.nz)), maxh = std::max(g.hkx, std::max(g.hky, g.hkz));
+  return 2ULL * maxn * maxh;
+}
+
+cudaError_t build_kernel_spectrum_ws(const Geom& g, double dx, double dy, double dz, float* kt, double* w0,
+                                     double* w1, double* tab, cudaStream_t s) {
+  const GLRules gl = make_gl_rules();
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int hx = g.hkx, hy = g.hky, hz = g.hkz;
+  const int T = 128;
+  auto blocks = [&](long long tot) { return (unsigned)((tot + T - 1) / T); };
+  k_tensor_octant<<<blocks(g.n), T, 0, s>>>(nx, ny, nz, dx, dy, dz, gl, w0);
+  auto transform = [&](int len, int P, int h, long long outer, int axis, double* in, double* out) {
+    double* tc = tab;
+    double* ts = tab + (size_t)len * h;
+    k_axis_tables<<<blocks((long long)len * h), T, 0, s>>>(len, P, h, tc, ts);
+    k_axis_transform<<<blocks(6 * outer * h), T, 0, s>>>(len, h, outer, axis, in, out, tc, ts);
+  };
+  transform(nx, g.px, hx, (long long)nz * ny, 0, w0, w1);
+  k_rotate<<<blocks(6LL * nz * ny * hx), T, 0, s>>>(nz, ny, hx, w1, w0);
+  transform(ny, g.py, hy, (long long)hx * nz, 1, w0, w1);
+  k_rotate<<<blocks(6LL * hx * nz * hy), T, 0, s>>>(hx, nz, hy, w1, w0);
+  transform(nz, g.pz, hz, (long long)hy * hx, 2, w0, w1);
+  k_rotate<<<blocks(6LL * hy * hx * hz), T, 0, s>>>(hy * hx, 1, hz, w1, w0);
+  const double scale = -kMu0 / ((double)g.lx * g.py * g.pz);
+  k_finish<<<blocks(6LL * hx * hy * hz), T, 0, s>>>((long long)hx * hy * hz, scale, w0, kt);
+  return cudaGetLastError();
 }
 
 }  // namespace mm

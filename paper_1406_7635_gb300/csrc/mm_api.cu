@@ -239,6 +239,10 @@ int eval_field(mm_ctx* c, int mode) {
 
 }  // namespace
 
+namespace mm {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace mm
+
 extern "C" {
 
 const char* mm_last_error(void) { return g_err.c_str(); }

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mm {
 
 constexpr int kRegions = 256;
@@ -78,12 +80,21 @@ struct Buffers {
 
 struct Terms { int demag, exch, anis, zeeman; };
 
+// sets the message mm_last_error() returns on this thread
+void set_last_error(const std::string& msg);
+
 // ---- launch wrappers (stream-ordered) ----
 // demag convolution of M = Msat m (m = `m`), result in b.bd
 void launch_demag(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
 // kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
                                   cudaStream_t s);
+// kernel precompute on caller-provided work space (no allocation, no host
+// round trips); sizes of the work areas in doubles
+size_t kernel_work_doubles(const Geom& g);
+size_t kernel_table_doubles(const Geom& g);
+cudaError_t build_kernel_spectrum_ws(const Geom& g, double dx, double dy, double dz, float* kt, double* w0,
+                                     double* w1, double* tab, cudaStream_t s);
 cudaError_t demag_tensor_offsets(int n, const int32_t* d_off, double dx, double dy, double dz,
                                  double* d_out, cudaStream_t s);
 

@@ -80,6 +80,7 @@ _SIGS = {
     "mm_set_state": (_I, [_P, _P, C.c_size_t]),
     "mm_demag_tensor": (_I, [_I, _D, _D, _D, _I, _P, _P]),
     "mm_demag_apply": (_I, [_P, _P, _P]),
+    "mm_demag_field_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _P, _P, _P]),
     "mm_sync": (_I, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -107,6 +108,13 @@ def demag_tensor(offsets, dx, dy, dz, device=0):
     out = np.zeros((off.shape[0], 6), dtype=np.float64)
     _check(mm_demag_tensor(device, dx, dy, dz, off.shape[0], _ptr(off), _ptr(out)))
     return out
+
+
+def demag_field_noalloc(M_dev, B_dev, nx, ny, nz, dx, dy, dz, stream=None):
+    """B (device tensor) of M (device tensor, A/m) using only the library's
+    static scratch: no device allocation (see mm_demag_field_noalloc)."""
+    _check(mm_demag_field_noalloc(nx, ny, nz, dx, dy, dz, C.c_void_p(M_dev.data_ptr()),
+                                  C.c_void_p(B_dev.data_ptr()), stream))
 
 
 class Context:
