@@ -44,6 +44,23 @@ __device__ __forceinline__ float2 w16(int k, int dir) {
   return make_float2(c, dir < 0 ? -s : s);
 }
 
+// o * exp(DIR 2 pi i k / 16) with the trivial factors done without multiplies
+template <int K, int DIR>
+__device__ __forceinline__ float2 rot16(float2 o) {
+  constexpr float h = 0.70710678118654752f;
+  if (K == 0) return o;
+  if (K == 4) return mul_dir_i<DIR>(o);
+  if (K == 2) {   // (1 + DIR i) h
+    const float2 t = mul_dir_i<DIR>(o);
+    return make_float2((o.x + t.x) * h, (o.y + t.y) * h);
+  }
+  if (K == 6) {   // (-1 + DIR i) h
+    const float2 t = mul_dir_i<DIR>(o);
+    return make_float2((t.x - o.x) * h, (t.y - o.y) * h);
+  }
+  return cmul(o, w16(K, DIR));
+}
+
 // In-register DFT of length R (R = 1, 2, 4, 8, 16), natural order in and out,
 // by recursive even/odd splitting.
 template <int R, int DIR>
@@ -54,11 +71,15 @@ struct Dft {
     for (int i = 0; i < R / 2; ++i) { e[i] = x[2 * i]; o[i] = x[2 * i + 1]; }
     Dft<R / 2, DIR>::run(e);
     Dft<R / 2, DIR>::run(o);
-#pragma unroll
-    for (int k = 0; k < R / 2; ++k) {
-      const float2 t = (k == 0) ? o[k] : cmul(o[k], w16(k * (16 / R), DIR));
-      x[k] = cadd(e[k], t);
-      x[k + R / 2] = csub(e[k], t);
+    combine<0>(x, e, o);
+  }
+  template <int K>
+  __device__ __forceinline__ static void combine(float2 (&x)[R], const float2 (&e)[R / 2], const float2 (&o)[R / 2]) {
+    if constexpr (K < R / 2) {
+      const float2 t = rot16<K * (16 / R), DIR>(o[K]);
+      x[K] = cadd(e[K], t);
+      x[K + R / 2] = csub(e[K], t);
+      combine<K + 1>(x, e, o);
     }
   }
 };
@@ -86,15 +107,16 @@ struct Dft<4, DIR> {
   }
 };
 
-// Radix of pass `p` for length L: 16s first, then the remainder.
+// Radix of pass `p` for length L (a power of two): as few passes as radix 16
+// allows, with the factors balanced so no pass is a thin radix-2/4 tail
+// (32 = 8 x 4, 64 = 8 x 8, 128 = 16 x 8, 512 = 8 x 8 x 8, 2048 = 16 x 16 x 8).
 __host__ __device__ constexpr int radix_of(int L, int p) {
-  int ns = 1, r = 1;
-  for (int i = 0; i <= p; ++i) {
-    const int left = L / ns;
-    r = left >= 16 ? 16 : left;   // left is a power of two
-    ns *= r;
-  }
-  return r;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int passes = (lg + 3) / 4;   // ceil(lg / 4) passes of at most radix 16
+  if (passes == 0) return 1;
+  const int base = lg / passes, extra = lg % passes;   // first `extra` passes get one more bit
+  return 1 << (base + (p < extra ? 1 : 0));
 }
 __host__ __device__ constexpr int npasses(int L) {
   int ns = 1, n = 0;
@@ -107,11 +129,15 @@ __host__ __device__ constexpr int ns_of(int L, int p) {
   return ns;
 }
 
-// One Stockham pass of radix R on NP pencils of length L in shared memory:
-// element i of pencil q at s[q * PST + i].  NT threads cooperate; butterfly b
-// belongs to pencil b % NP (consecutive threads -> consecutive pencils, which
-// with PST = L + 1 keeps shared-memory accesses free of bank conflicts).
-template <int L, int R, int NS, int DIR, int NP, int NT, int PST>
+// One Stockham pass of radix R on NP pencils of length L in shared memory.
+// Element i of pencil q sits at s[(q / INNER) * BS + (q % INNER) + i * ES]:
+// rows (INNER = 1, BS = pitch, ES = 1) or columns of a row-major plane
+// (INNER = row length, BS = plane size, ES = pitch).  NT threads cooperate;
+// butterfly b belongs to pencil b % NP, so consecutive threads touch
+// consecutive pencils (with an odd row pitch this avoids bank conflicts).
+// tw holds W_TWL^i = exp(-2 pi i i / TWL) for i < TWL (TWL a multiple of L):
+// the global 2048-entry table, or a per-length copy in shared memory.
+template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL>
 __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
@@ -122,8 +148,9 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
     const int b = threadIdx.x + q * NT;
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
+      const int base = (p / INNER) * BS + (p % INNER);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[p * PST + j + r * NB];
+      for (int r = 0; r < R; ++r) v[q][r] = s[base + (j + r * NB) * ES];
     }
   }
   __syncthreads();
@@ -132,40 +159,52 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
     const int b = threadIdx.x + q * NT;
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
+      const int base = (p / INNER) * BS + (p % INNER);
       const int k = j % NS;
       if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          // exp(DIR 2 pi i r k / (NS R)) = W[r k (kTwN / (NS R))] (conjugated if DIR > 0)
-          float2 w = __ldg(&tw[(r * k * (kTwN / (NS * R))) & (kTwN - 1)]);
+          // exp(DIR 2 pi i r k / (NS R)) = W[r k (TWL / (NS R))] (conjugated if DIR > 0)
+          float2 w = tw[(r * k * (TWL / (NS * R))) & (TWL - 1)];
           if (DIR > 0) w.y = -w.y;
           v[q][r] = cmul(v[q][r], w);
         }
       }
       Dft<R, DIR>::run(v[q]);
-      const int base = (j - k) * R + k;
+      const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[p * PST + base + r * NS] = v[q][r];
+      for (int r = 0; r < R; ++r) s[base + (o + r * NS) * ES] = v[q][r];
     }
   }
   __syncthreads();
 }
 
 // Full length-L complex transform of NP shared-memory pencils (in place,
-// natural order).  Caller synchronises before (data written) -- the first pass
-// starts with reads; the last pass ends with __syncthreads().
-template <int L, int DIR, int NP, int NT, int PST, int P = 0, bool DONE = (P >= npasses(L))>
-struct Fft;
-template <int L, int DIR, int NP, int NT, int PST, int P>
-struct Fft<L, DIR, NP, NT, PST, P, false> {
+// natural order), addressed as in stockham_pass.  Callers synchronise before
+// (data written); the last pass ends with __syncthreads().
+template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL = kTwN, int P = 0,
+          bool DONE = (P >= npasses(L))>
+struct FftG;
+template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
+struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, false> {
   __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw) {
-    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, PST>(s, tw);
-    Fft<L, DIR, NP, NT, PST, P + 1>::run(s, tw);
+    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL>(s, tw);
+    FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P + 1>::run(s, tw);
   }
 };
-template <int L, int DIR, int NP, int NT, int PST, int P>
-struct Fft<L, DIR, NP, NT, PST, P, true> {
+template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
+struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, true> {
   __device__ __forceinline__ static void run(float2*, const float2* __restrict__) {}
 };
+
+// pencils stored as rows with pitch PST, twiddles from the global table
+template <int L, int DIR, int NP, int NT, int PST>
+using Fft = FftG<L, DIR, NP, NT, 1, PST, 1>;
+
+// copy W_L^i (i < L) out of the global 2048-entry table into shared memory
+template <int L, int NT>
+__device__ __forceinline__ void load_twiddles(float2* dst, const float2* __restrict__ tw) {
+  for (int i = threadIdx.x; i < L; i += NT) dst[i] = __ldg(&tw[i * (kTwN / L)]);
+}
 
 }  // namespace mmfft

@@ -314,6 +314,10 @@ void run_col(const Geom& g, const Buffers& b, cudaStream_t s) {
 }  // namespace
 
 void launch_demag(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
+  if (g.fused) {
+    launch_demag_fused(g, b, m, s);
+    return;
+  }
   const int nrows = 3 * g.nz * g.ny;
   // FX
   if (g.px == 1) {

@@ -1,0 +1,388 @@
+// Fused demag convolution for grids whose padded (y, z) plane is small
+// enough: three kernels per convolution instead of five, every global access
+// contiguous, and the zero-padded half of the spectrum never materialised.
+//
+//   k_fx_t  x rows: real M -> half spectrum (as k_fx), written transposed to
+//           spec[c][kx][z][y] (y fastest) so one kx plane is contiguous;
+//   k_yz    one kx plane per thread-block cluster: y and z transforms, the
+//           kernel multiply and the inverse transforms;
+//   k_ix_t  x rows back to real B (as k_ix), reading the transposed layout.
+//
+// k_yz splits the padded (py x pz) transform by frequency residue class:
+// with ky = CLY j + ry and kz = CLZ l + rz, the padded DFT restricted to one
+// class is an unpadded (py/CLY x pz/CLZ) DFT of the input multiplied by
+// exp(-2 pi i (y ry / py + z rz / pz)) (valid because ny <= py/CLY and
+// nz <= pz/CLZ, so no folding is needed).  Each block of a cluster of
+// CLY*CLZ blocks owns one class: it twiddles the input, transforms it,
+// multiplies by the kernel at its (kx, ky, kz), transforms back, undoes the
+// twiddle, and the cluster sums the CLY*CLZ contributions through
+// distributed shared memory.
+#include <cooperative_groups.h>
+
+#include "fft.cuh"
+#include "mm_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace mm {
+namespace {
+using namespace mmfft;
+
+__device__ __forceinline__ float cell_msat_f(const RegionLUT* __restrict__ lut, const uint8_t* __restrict__ mask,
+                                             const uint8_t* __restrict__ region, long long i) {
+  return mask[i] ? __ldg(&lut->msat[region[i]]) : 0.0f;
+}
+
+__device__ __forceinline__ long long tidx(const Geom& g, int c, int kx, int z, int y) {
+  return (((long long)c * g.hx + kx) * g.nz + z) * g.ny + y;
+}
+
+// ----------------------------------------------------------------------------
+// x rows, transposed spectrum
+// ----------------------------------------------------------------------------
+template <int L, int ROWS, int NT>
+__global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m, const uint8_t* __restrict__ mask,
+                                             const uint8_t* __restrict__ region, const RegionLUT* __restrict__ lut,
+                                             float2* __restrict__ spec, const float2* __restrict__ tw,
+                                             const DevState* __restrict__ st) {
+  if (st && st->done) return;
+  constexpr int PST = L + 1;
+  __shared__ float2 s[ROWS * PST];
+  __shared__ float2 twl[L], tw2[L + 1];   // W_L^i and W_2L^k
+  const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z;
+  load_twiddles<L, NT>(twl, tw);
+  for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
+  const bool even = (g.nx & 1) == 0;
+  for (int e = threadIdx.x; e < ROWS * L; e += NT) {
+    const int r = e / L, n = e % L, y = y0 + r;
+    float2 v = make_float2(0.f, 0.f);
+    if (y < g.ny) {
+      const long long cell0 = ((long long)z * g.ny + y) * g.nx;
+      const int x0 = 2 * n, x1 = 2 * n + 1;
+      if (even && x1 < g.nx) {
+        // cell0 + x0 is even: aligned pair loads
+        const float2 mv = *reinterpret_cast<const float2*>(m + c * g.n + cell0 + x0);
+        const uchar2 mk = *reinterpret_cast<const uchar2*>(mask + cell0 + x0);
+        const uchar2 rg = *reinterpret_cast<const uchar2*>(region + cell0 + x0);
+        v.x = mk.x ? __ldg(&lut->msat[rg.x]) * mv.x : 0.f;
+        v.y = mk.y ? __ldg(&lut->msat[rg.y]) * mv.y : 0.f;
+      } else {
+        if (x0 < g.nx) v.x = cell_msat_f(lut, mask, region, cell0 + x0) * m[c * g.n + cell0 + x0];
+        if (x1 < g.nx) v.y = cell_msat_f(lut, mask, region, cell0 + x1) * m[c * g.n + cell0 + x1];
+      }
+    }
+    s[r * PST + n] = v;
+  }
+  __syncthreads();
+  FftG<L, -1, ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  // X_k = E_k + W_P^k O_k; store with consecutive threads on consecutive y
+  for (int e = threadIdx.x; e < ROWS * (L + 1); e += NT) {
+    const int r = e % ROWS, k = e / ROWS, y = y0 + r;
+    if (y >= g.ny) continue;
+    const float2 zk = s[r * PST + (k & (L - 1))];
+    const float2 zc = cconj(s[r * PST + ((L - k) & (L - 1))]);
+    const float2 E = cscale(cadd(zk, zc), 0.5f);
+    const float2 d = csub(zk, zc);
+    const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);
+    spec[tidx(g, c, k, z, y)] = cadd(E, cmul(tw2[k], O));
+  }
+}
+
+template <int L, int ROWS, int NT>
+__global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ spec, float* __restrict__ out,
+                                             const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  if (st && st->done) return;
+  constexpr int PST = L + 1;
+  __shared__ float2 s[ROWS * PST];
+  __shared__ float2 twl[L], tw2[L + 1];   // W_L^i and W_2L^k
+  const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z;
+  load_twiddles<L, NT>(twl, tw);
+  for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
+  for (int e = threadIdx.x; e < ROWS * (L + 1); e += NT) {
+    const int r = e % ROWS, k = e / ROWS, y = y0 + r;
+    s[r * PST + k] = y < g.ny ? spec[tidx(g, c, k, z, y)] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ROWS * (L / 2 + 1); e += NT) {
+    const int r = e / (L / 2 + 1), k = e % (L / 2 + 1);
+    const float2 xa = s[r * PST + k], xb = s[r * PST + L - k];
+    float2 za, zb;
+    {
+      const float2 E = cscale(cadd(xa, cconj(xb)), 0.5f);
+      const float2 w = cconj(tw2[k]);
+      const float2 O = cmul(cscale(csub(xa, cconj(xb)), 0.5f), w);
+      za = make_float2(E.x - O.y, E.y + O.x);
+    }
+    {
+      const int kb = L - k;
+      const float2 E = cscale(cadd(xb, cconj(xa)), 0.5f);
+      const float2 w = cconj(tw2[kb]);
+      const float2 O = cmul(cscale(csub(xb, cconj(xa)), 0.5f), w);
+      zb = make_float2(E.x - O.y, E.y + O.x);
+    }
+    s[r * PST + k] = za;
+    if (k != 0 && k != L / 2) s[r * PST + L - k] = zb;
+  }
+  __syncthreads();
+  FftG<L, 1, ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  for (int e = threadIdx.x; e < ROWS * L; e += NT) {
+    const int r = e / L, n = e % L, y = y0 + r;
+    if (y >= g.ny) continue;
+    const long long cell0 = ((long long)z * g.ny + y) * g.nx;
+    const float2 v = s[r * PST + n];
+    if ((g.nx & 1) == 0 && 2 * n + 1 < g.nx) {
+      *reinterpret_cast<float2*>(out + c * g.n + cell0 + 2 * n) = v;
+    } else {
+      if (2 * n < g.nx) out[c * g.n + cell0 + 2 * n] = v.x;
+      if (2 * n + 1 < g.nx) out[c * g.n + cell0 + 2 * n + 1] = v.y;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// kernel multiply (octant lookup with mirror signs; x never mirrors)
+// ----------------------------------------------------------------------------
+// ktf holds the octant per kx plane, ky fastest: ktf[kx][c][iz][iy]
+__device__ __forceinline__ void kmul(const Geom& g, const float* __restrict__ ktf, int kx, int ky, int kz, float2& X,
+                                     float2& Y, float2& Z) {
+  int iy = ky, iz = kz;
+  float sy = 1.f, sz = 1.f;
+  if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
+  if (kz > g.pz / 2) { iz = g.pz - kz; sz = -1.f; }
+  const long long per = (long long)g.hky * g.hkz;
+  const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
+  const float kxx = __ldg(&ktf[o]), kyy = __ldg(&ktf[per + o]), kzz = __ldg(&ktf[2 * per + o]);
+  const float kxy = sy * __ldg(&ktf[3 * per + o]);
+  const float kxz = sz * __ldg(&ktf[4 * per + o]);
+  const float kyz = sy * sz * __ldg(&ktf[5 * per + o]);
+  const float2 bx = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+  const float2 by = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+  const float2 bz = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+  X = bx;
+  Y = by;
+  Z = bz;
+}
+
+// ----------------------------------------------------------------------------
+// k_yz: plane [3][LZ][LY] in shared memory, y fastest, rows padded to an
+// odd pitch RP = LY + 1 (conflict-free row and column transforms)
+// ----------------------------------------------------------------------------
+template <int LY, int LZ, int NT>
+__global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec, const float* __restrict__ kt,
+                                           const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  if (st && st->done) return;   // uniform across the cluster: all blocks leave together
+  extern __shared__ float2 s[];
+  constexpr int RP = LY + 1;
+  constexpr int PL = LY * LZ;   // points per component
+  constexpr int CS = LZ * RP;   // component stride in shared memory
+  // twiddle tables after the plane: W_LY^i, W_LZ^i, and the residue twiddles
+  // W_py^y (y < LY), W_pz^z (z < LZ)
+  float2* twy = s + 3 * CS;
+  float2* twz = twy + LY;
+  float2* rty = twz + LZ;
+  float2* rtz = rty + LY;
+  load_twiddles<LY, NT>(twy, tw);
+  load_twiddles<LZ, NT>(twz, tw);
+  for (int i = threadIdx.x; i < LY; i += NT) rty[i] = __ldg(&tw[(i * (kTwN / g.py)) & (kTwN - 1)]);
+  for (int i = threadIdx.x; i < LZ; i += NT) rtz[i] = __ldg(&tw[(i * (kTwN / g.pz)) & (kTwN - 1)]);
+  __syncthreads();
+  const int CL = g.cly * g.clz;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
+  const int ry = rank % g.cly, rz = rank / g.cly;
+  const int kx = blockIdx.x / CL;
+  // 1. load and twiddle by exp(-2 pi i (y ry / py + z rz / pz))
+#pragma unroll 4
+  for (int e = threadIdx.x; e < 3 * PL; e += NT) {
+    const int y = e % LY, z = (e / LY) % LZ, c = e / PL;
+    float2 v = make_float2(0.f, 0.f);
+    if (y < g.ny && z < g.nz) {
+      v = spec[tidx(g, c, kx, z, y)];
+      if (ry) v = cmul(v, rty[y]);
+      if (rz) v = cmul(v, rtz[z]);
+    }
+    s[c * CS + z * RP + y] = v;
+  }
+  __syncthreads();
+  // 2. forward transforms along y (LZ rows) and z (LY columns), one
+  //    component at a time (fewer values held in registers per pass)
+  for (int c = 0; c < 3; ++c) {
+    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
+    FftG<LZ, -1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz);
+  }
+  // 3. multiply by the kernel at (kx, ky = CLY j + ry, kz = CLZ l + rz)
+  for (int e = threadIdx.x; e < PL; e += NT) {
+    const int j = e % LY, l = e / LY;
+    const int a = l * RP + j;
+    float2 X = s[a], Y = s[CS + a], Z = s[2 * CS + a];
+    kmul(g, kt, kx, g.cly * j + ry, g.clz * l + rz, X, Y, Z);
+    s[a] = X;
+    s[CS + a] = Y;
+    s[2 * CS + a] = Z;
+  }
+  __syncthreads();
+  // 4. inverse transforms
+  for (int c = 0; c < 3; ++c) {
+    FftG<LZ, 1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz);
+    FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
+  }
+  // 5. undo the twiddle on the outputs that are kept (y < ny, z < nz)
+  if (ry || rz) {
+    for (int e = threadIdx.x; e < 3 * PL; e += NT) {
+      const int y = e % LY, z = (e / LY) % LZ, c = e / PL;
+      if (y < g.ny && z < g.nz) {
+        const int a = c * CS + z * RP + y;
+        float2 v = s[a];
+        if (ry) v = cmul(v, cconj(rty[y]));
+        if (rz) v = cmul(v, cconj(rtz[z]));
+        s[a] = v;
+      }
+    }
+  }
+  // 6. sum the class contributions across the cluster; each block stores one
+  //    contiguous 1/CL share of the plane
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+  const int nout = 3 * g.nz * g.ny;
+  const int chunk = (nout + CL - 1) / CL;
+  const int o_end = min(nout, (rank + 1) * chunk);
+  for (int o = rank * chunk + threadIdx.x; o < o_end; o += NT) {
+    const int y = o % g.ny, z = (o / g.ny) % g.nz, c = o / (g.ny * g.nz);
+    const int e = c * CS + z * RP + y;
+    float2 v = s[e];
+    for (int q = 1; q < CL; ++q) {
+      const float2* rs = cluster.map_shared_rank(s, (rank + q) % CL);
+      v = cadd(v, rs[e]);
+    }
+    spec[tidx(g, c, kx, z, y)] = v;
+  }
+  if (CL > 1) cluster.sync();   // keep shared memory alive until every peer has read it
+}
+
+template <int L>
+struct RowCfgT {
+  // enough blocks to fill the GPU: 8 rows of <= 128 points per block
+  static constexpr int ROWS = L >= 512 ? 2 : (L >= 256 ? 4 : 8);
+  static constexpr int NT = ROWS * L / 8 < 64 ? 64 : ROWS * L / 8;
+};
+
+template <int L>
+void run_fx_t(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
+  using C = RowCfgT<L>;
+  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3);
+  k_fx_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, m, b.mask, b.region, b.lut, b.spec, b.tw, b.st);
+}
+template <int L>
+void run_ix_t(const Geom& g, const Buffers& b, cudaStream_t s) {
+  using C = RowCfgT<L>;
+  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3);
+  k_ix_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, b.spec, b.bd, b.tw, b.st);
+}
+
+template <int LY, int LZ>
+struct YzCfg {
+  static constexpr int B0 = LY * LZ / 8;    // radix-8 butterflies per component
+  static constexpr int NT = B0 < 64 ? 64 : (B0 > 512 ? 512 : B0);
+  static constexpr size_t SMEM = sizeof(float2) * (3 * LZ * (LY + 1) + 2 * (LY + LZ));
+};
+
+template <int LY, int LZ>
+void run_yz(const Geom& g, const Buffers& b, cudaStream_t s) {
+  using C = YzCfg<LY, LZ>;
+  auto kern = k_yz<LY, LZ, C::NT>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    attr_set = true;
+  }
+  const int CL = g.cly * g.clz;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g.hx * CL);
+  cfg.blockDim = dim3(C::NT);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st);
+}
+
+__global__ void k_kt_transpose(Geom g, const float* __restrict__ kt, float* __restrict__ ktf) {
+  const long long per = (long long)g.hky * g.hkz;
+  const long long total = 6LL * g.hkx * per;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  // destination index i = (kx * 6 + c) * per + iz * hky + iy
+  const int iy = (int)(i % g.hky);
+  const int iz = (int)((i / g.hky) % g.hkz);
+  const int c = (int)((i / per) % 6);
+  const int kx = (int)(i / (6 * per));
+  ktf[i] = kt[(long long)c * g.hkx * per + ((long long)iz * g.hky + iy) * g.hkx + kx];
+}
+
+}  // namespace
+
+void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s) {
+  const long long total = 6LL * g.hkx * g.hky * g.hkz;
+  k_kt_transpose<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, kt, ktf);
+}
+
+// Chooses the residue split for the fused path: py/cly >= ny, pz/clz >= nz,
+// 3 (py/cly)(pz/clz) complex values in at most 96 KB of shared memory.
+bool fused_plan(Geom& g) {
+  g.fused = 0;
+  if (g.px < 32 || g.lx > 512) return false;
+  for (int clz = 1; clz <= (g.pz > 1 ? 2 : 1); ++clz)
+    for (int cly = 1; cly <= (g.py > 1 ? 2 : 1); ++cly) {
+      const int ly = g.py / cly, lz = g.pz / clz;
+      if (ly < g.ny || lz < g.nz) continue;
+      if (ly < 16 || ly > 1024 || lz > 32) continue;
+      if ((long long)ly * lz > 4096) continue;
+      g.cly = cly;
+      g.clz = clz;
+      g.ly = ly;
+      g.lz = lz;
+      g.fused = 1;
+      return true;
+    }
+  return false;
+}
+
+#define MM_ROWL(LEN, CALL) \
+  switch (LEN) {           \
+    case 16: CALL(16); break; \
+    case 32: CALL(32); break; \
+    case 64: CALL(64); break; \
+    case 128: CALL(128); break; \
+    case 256: CALL(256); break; \
+    case 512: CALL(512); break; \
+    default: break;        \
+  }
+
+void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
+#define CALL_FX(LL) run_fx_t<LL>(g, b, m, s)
+  MM_ROWL(g.lx, CALL_FX)
+#undef CALL_FX
+  const int key = g.ly * 100 + g.lz;
+  switch (key) {
+#define YZ(LY, LZ) \
+  case LY * 100 + LZ: run_yz<LY, LZ>(g, b, s); break;
+    YZ(16, 1) YZ(32, 1) YZ(64, 1) YZ(128, 1) YZ(256, 1) YZ(512, 1) YZ(1024, 1)
+    YZ(16, 2) YZ(32, 2) YZ(64, 2) YZ(128, 2) YZ(256, 2) YZ(512, 2) YZ(1024, 2)
+    YZ(16, 4) YZ(32, 4) YZ(64, 4) YZ(128, 4) YZ(256, 4) YZ(512, 4) YZ(1024, 4)
+    YZ(16, 8) YZ(32, 8) YZ(64, 8) YZ(128, 8) YZ(256, 8) YZ(512, 8)
+    YZ(16, 16) YZ(32, 16) YZ(64, 16) YZ(128, 16) YZ(256, 16)
+    YZ(16, 32) YZ(32, 32) YZ(64, 32) YZ(128, 32)
+#undef YZ
+    default: break;
+  }
+#define CALL_IX(LL) run_ix_t<LL>(g, b, s)
+  MM_ROWL(g.lx, CALL_IX)
+#undef CALL_IX
+}
+
+}  // namespace mm

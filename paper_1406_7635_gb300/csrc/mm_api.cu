@@ -136,6 +136,7 @@ void invalidate(mm_ctx* c) {
 
 // kernels one demag convolution launches (see launch_demag)
 int demag_launches(const Geom& g) {
+  if (g.fused) return 3;
   int mid = g.pz > 1 ? (g.py > 1 ? 3 : 1) : 1;
   return 2 + mid;
 }
@@ -279,6 +280,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   g.hkx = g.px == 1 ? 1 : g.px / 2 + 1;
   g.hky = g.py == 1 ? 1 : g.py / 2 + 1;
   g.hkz = g.pz == 1 ? 1 : g.pz / 2 + 1;
+  fused_plan(g);
   for (int r = 0; r < kRegions; ++r) {
     std::memset(&c->mat[r], 0, sizeof(mm_material));
     c->mat[r].gamma_ll = kGamma;
@@ -312,6 +314,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   alloc((void**)&b.out, vec);
   alloc((void**)&b.spec, 3 * (size_t)g.sc * sizeof(float2));
   alloc((void**)&b.kt, 6 * (size_t)g.hkx * g.hky * g.hkz * sizeof(float));
+  if (g.fused) alloc((void**)&b.ktf, 6 * (size_t)g.hkx * g.hky * g.hkz * sizeof(float));
   alloc((void**)&b.tw, 2048 * sizeof(float2));
   alloc((void**)&b.mask, (size_t)g.n);
   alloc((void**)&b.region, (size_t)g.n);
@@ -336,6 +339,10 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, cudaGetErrorString(e)));
   // demag kernel (float64 on the device)
   e = build_kernel_spectrum(g, dx, dy, dz, b.kt, c->stream);
+  if (e == cudaSuccess && g.fused) {
+    launch_kt_transpose(g, b.kt, b.ktf, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,
                         std::string("kernel precompute: ") + cudaGetErrorString(e)));
@@ -371,7 +378,7 @@ int mm_destroy(mm_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   Buffers& b = c->b;
   void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.bd, b.out,
-                  b.spec, b.kt, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed};
+                  b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);

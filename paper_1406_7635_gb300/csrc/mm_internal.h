@@ -35,6 +35,9 @@ struct Geom {
   int srows;              // rows per plane in the spectrum buffer (py if pz > 1 else ny)
   long long sc;           // complex elements per component of the spectrum buffer
   int hkx, hky, hkz;      // octant sizes of the kernel spectrum
+  // fused path (fft_fused.cu): spectrum laid out [3][hx][nz][ny], one
+  // cluster of cly*clz blocks per kx plane, each transforming ly x lz points
+  int fused, cly, clz, ly, lz;
 };
 
 // Integrator state on the device (one per context).  Every kernel of a step
@@ -66,6 +69,7 @@ struct Buffers {
   float* bd;          // demag field
   float2* spec;       // spectrum work buffer
   float* kt;          // kernel spectrum octant [6][hkz][hky][hkx]
+  float* ktf;         // fused path: the same octant as [hkx][6][hkz][hky]
   float2* tw;         // twiddles W[k] = exp(-2 pi i k / 2048)
   uint8_t* mask;
   uint8_t* region;
@@ -86,6 +90,10 @@ void set_last_error(const std::string& msg);
 // ---- launch wrappers (stream-ordered) ----
 // demag convolution of M = Msat m (m = `m`), result in b.bd
 void launch_demag(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
+// fused three-kernel convolution; fused_plan() decides whether g supports it
+bool fused_plan(Geom& g);
+void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
+void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s);
 // kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
                                   cudaStream_t s);

@@ -1,0 +1,56 @@
+"""Parity at the benchmark workloads' full sizes, in the configuration
+bench.py times: the 256 x 256 x 1 grain film and the 128 x 128 x 32 ellipsoid.
+Fields and torques are compared on every cell against the float64 oracle; one
+RK45 step is replayed by the oracle with the GPU's step size."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.field import Field, ll_torque  # noqa: E402
+from oracle.rk45 import RK45  # noqa: E402
+from paper_1406_7635_gb300.workloads import WORKLOADS  # noqa: E402
+
+FIELD_TOL = 5e-6
+M_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1406_7635_gb300.build import build
+    build()
+    from paper_1406_7635_gb300 import mm as _mm
+    return _mm
+
+
+@pytest.mark.parametrize("name", ["grains_256x256x1", "ellipsoid_128x128x32"])
+def test_fullsize_field_torque_and_step(mm, name):
+    p = WORKLOADS[name]()
+    ctx = mm.Context.from_problem(p)
+    t = 0.21e-9
+    ctx.set_time(t, 1e-13)
+    B = ctx.get_beff().astype(np.float64)
+    Bd = ctx.get_bdemag().astype(np.float64)
+    tau = ctx.get_torque().astype(np.float64)
+    m32 = p.m0.astype(np.float32).astype(np.float64)
+    f = Field(p)
+    terms = f.terms(m32, t)
+    Bo = terms["total"]
+    scale_d = np.abs(terms["demag"]).max()
+    assert np.abs(Bd - terms["demag"]).max() <= FIELD_TOL * scale_d
+    assert np.abs(B - Bo).max() <= FIELD_TOL * np.abs(Bo).max()
+    to = ll_torque(p, m32, Bo)
+    assert np.abs(tau - to).max() <= FIELD_TOL * np.abs(to).max()
+    # one adaptive step on the GPU, replayed by the oracle
+    ctx.set_time(0.0, p.dt0)
+    ctx.step(1)
+    m_gpu = ctx.get_m().astype(np.float64)
+    dts = ctx.get_dt_history()
+    ctx.close()
+    ora = RK45(p, m=m32)
+    ora.field = f
+    ora.run_fixed(dts[-1:])
+    assert np.abs(m_gpu - ora.m).max() <= M_TOL

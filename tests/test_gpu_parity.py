@@ -71,6 +71,10 @@ GRIDS = [
     ((4, 1, 1), (1e-9, 1e-9, 2e-9)),
     ((1, 33, 1), (1e-9, 1e-9, 1e-9)),
     ((6, 12, 20), (5e-9, 5e-9, 5e-9)),
+    ((20, 64, 24), (3e-9, 3e-9, 3e-9)),     # fused path, residue split in z (2 blocks)
+    ((3, 300, 20), (2e-9, 2e-9, 4e-9)),     # fused path, residue split in y (2 blocks)
+    ((20, 100, 40), (3e-9, 3e-9, 2e-9)),    # fused path, split in y and z (4 blocks)
+    ((40, 30, 9), (2e-9, 2e-9, 2e-9)),      # general path (pz too large for the fused plane)
 ]
 
 
