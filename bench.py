@@ -233,7 +233,61 @@ def run_ours(args, rank, world, local_rank):
     }
     if side:
         out["film"] = side
+    if args.batch:
+        out["batch"] = run_batch(args, local_rank)
     return out
+
+
+def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
+    """The batched form: 512 independent instances of four grid sizes, each
+    with its own adaptive step, advanced to t_end by one graph launch; against
+    the plain single-instance path run one instance after another on a
+    stratified sample (seq_per_shape instances of each grid size),
+    extrapolated by the number of instances of each size."""
+    import torch
+    from paper_1406_7635_gb300 import mm
+    from paper_1406_7635_gb300.workloads import batch_instances, problem_from_instance
+    specs, m0s = batch_instances(512)
+    b = mm.Batch(specs, device=local_rank)
+    for i, m in enumerate(m0s):
+        b.set_m(i, m)
+    b.run(1e-15)                      # warm-up: builds and instantiates the graph
+    for i, m in enumerate(m0s):
+        b.set_m(i, m)
+    b.set_solver()                    # restart the step-size controller
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(t_end + 1e-15)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    stats = [b.get_stats(i) for i in range(len(specs))]
+    b.close()
+    cell_steps = sum(s["accepted"] * sp["nx"] * sp["ny"] * sp["nz"] for s, sp in zip(stats, specs))
+    shapes = {}
+    for i, sp in enumerate(specs):
+        shapes.setdefault((sp["nx"], sp["ny"], sp["nz"]), []).append(i)
+    seq_time = 0.0
+    for key, idx in shapes.items():
+        per = []
+        for i in idx[:seq_per_shape]:
+            p = problem_from_instance(specs[i], m0s[i])
+            ctx = mm.Context.from_problem(p, device=local_rank)
+            ctx.run(1e-15)
+            ctx.set_m(p.m0)
+            ctx.set_time(0.0, p.dt0)
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            ctx.run(t_end + 1e-15)
+            torch.cuda.synchronize()
+            per.append(time.perf_counter() - ts)
+            ctx.close()
+        seq_time += np.mean(per) * len(idx)
+    return {"workload": "batch512 (32x32x1, 64x32x1, 128x64x2, 96x96x4; 4 nm cells)", "instances": len(specs),
+            "t_end_s": t_end, "wall_s": wall, "instances_per_s": len(specs) / wall,
+            "cell_steps_per_s": cell_steps / wall, "accepted_steps_mean": float(np.mean([s["accepted"] for s in stats])),
+            "sequential_instances_per_s": len(specs) / seq_time,
+            "speedup_vs_sequential": seq_time / wall,
+            "sequential_sample": f"{seq_per_shape} instances per grid size, same t_end, extrapolated by count"}
 
 
 def oracle_cpu_run(name, budget_s, max_steps):
@@ -282,6 +336,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", dest="side", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = env_rank()

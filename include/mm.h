@@ -194,6 +194,44 @@ int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double dy, double 
 /* Blocks until the context's stream is idle. */
 int mm_sync(mm_ctx* ctx);
 
+/* ---- Batched simulations --------------------------------------------------
+ * Many independent simulations of uneven grid sizes advanced together, each
+ * with its own adaptive Dormand-Prince step (Sec. IV) and its own material and
+ * static applied field (demag + exchange + Zeeman, every cell magnetic, one
+ * material per instance).  Instances of the same grid and cell size share one
+ * demag kernel.  A run is one CUDA graph launch that repeats batched RK45
+ * attempts on the device until every instance reaches t_end. */
+typedef struct mm_batch mm_batch;
+typedef struct {
+  int nx, ny, nz;           /* grid (nx >= 17; the padded (y, z) plane of   */
+  double dx, dy, dz;        /* one grid must fit one thread-block cluster)  */
+  double msat, aex, alpha;  /* material (A/m, J/m, -)                       */
+  double gamma_ll;          /* rad/(T s); <= 0 means 1.7595e11              */
+  double bext[3];           /* static applied field (T)                     */
+} mm_instance_spec;
+
+/* Creates n instances (specs copied); m starts at zero: set it with
+ * mm_batch_set_m before running.  Defaults as in mm_create. */
+int mm_batch_create(mm_batch** out, int n, const mm_instance_spec* specs, int device,
+                    void* cuda_stream);
+int mm_batch_destroy(mm_batch* b);
+/* m of instance i, float32 SoA [3][nz][ny][nx] of that instance (host);
+ * normalised per cell on upload. */
+int mm_batch_set_m(mm_batch* b, int i, const float* m);
+int mm_batch_get_m(mm_batch* b, int i, float* m);
+/* Step control of every instance (as mm_set_solver). */
+int mm_batch_set_solver(mm_batch* b, double max_err, double headroom, double dt0,
+                        double dt_min, double dt_max);
+/* Advances every instance to t_end (last step shortened to land on it). */
+int mm_batch_run(mm_batch* b, double t_end);
+/* Counters of instance i; returns that instance's status (MM_OK or the error
+ * that stopped it). */
+int mm_batch_get_stats(mm_batch* b, int i, mm_stats* s);
+/* Accepted step sizes of instance i (the first 4096), as mm_get_dt_history. */
+int mm_batch_get_dt_history(mm_batch* b, int i, double* dts, int max, int* n);
+/* Number of shape classes (distinct grids) in the batch. */
+int mm_batch_num_classes(mm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,16 +40,24 @@ __device__ __forceinline__ long long tidx(const Geom& g, int c, int kx, int z, i
 // ----------------------------------------------------------------------------
 // x rows, transposed spectrum
 // ----------------------------------------------------------------------------
+// Batches: blockIdx.z = 3 * instance + component; instance i reads m + 3 n i,
+// writes spec + 3 hx nz ny i, takes Msat from inst_msat[i] (all cells
+// magnetic) when inst_msat is given, and is skipped once inst_done[i] is set.
 template <int L, int ROWS, int NT>
 __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m, const uint8_t* __restrict__ mask,
                                              const uint8_t* __restrict__ region, const RegionLUT* __restrict__ lut,
                                              float2* __restrict__ spec, const float2* __restrict__ tw,
-                                             const DevState* __restrict__ st) {
+                                             const DevState* __restrict__ st, BatchArgs ba) {
   if (st && st->done) return;
+  const int inst = blockIdx.z / 3;
+  if (ba.done && ba.done[(long long)inst * ba.done_stride]) return;
+  m += (long long)inst * 3 * g.n;
+  spec += (long long)inst * 3 * g.hx * g.nz * g.ny;
+  const float inst_ms = ba.msat ? ba.msat[inst] : 0.0f;
   constexpr int PST = L + 1;
   __shared__ float2 s[ROWS * PST];
   __shared__ float2 twl[L], tw2[L + 1];   // W_L^i and W_2L^k
-  const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z;
+  const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z % 3;
   load_twiddles<L, NT>(twl, tw);
   for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
   const bool even = (g.nx & 1) == 0;
@@ -59,7 +67,10 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
     if (y < g.ny) {
       const long long cell0 = ((long long)z * g.ny + y) * g.nx;
       const int x0 = 2 * n, x1 = 2 * n + 1;
-      if (even && x1 < g.nx) {
+      if (ba.msat) {
+        if (x0 < g.nx) v.x = inst_ms * m[c * g.n + cell0 + x0];
+        if (x1 < g.nx) v.y = inst_ms * m[c * g.n + cell0 + x1];
+      } else if (even && x1 < g.nx) {
         // cell0 + x0 is even: aligned pair loads
         const float2 mv = *reinterpret_cast<const float2*>(m + c * g.n + cell0 + x0);
         const uchar2 mk = *reinterpret_cast<const uchar2*>(mask + cell0 + x0);
@@ -90,12 +101,17 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
 
 template <int L, int ROWS, int NT>
 __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ spec, float* __restrict__ out,
-                                             const float2* __restrict__ tw, const DevState* __restrict__ st) {
+                                             const float2* __restrict__ tw, const DevState* __restrict__ st,
+                                             BatchArgs ba) {
   if (st && st->done) return;
+  const int inst = blockIdx.z / 3;
+  if (ba.done && ba.done[(long long)inst * ba.done_stride]) return;
+  out += (long long)inst * 3 * g.n;
+  spec += (long long)inst * 3 * g.hx * g.nz * g.ny;
   constexpr int PST = L + 1;
   __shared__ float2 s[ROWS * PST];
   __shared__ float2 twl[L], tw2[L + 1];   // W_L^i and W_2L^k
-  const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z;
+  const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z % 3;
   load_twiddles<L, NT>(twl, tw);
   for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
   for (int e = threadIdx.x; e < ROWS * (L + 1); e += NT) {
@@ -169,8 +185,14 @@ __device__ __forceinline__ void kmul(const Geom& g, const float* __restrict__ kt
 // ----------------------------------------------------------------------------
 template <int LY, int LZ, int NT>
 __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec, const float* __restrict__ kt,
-                                           const float2* __restrict__ tw, const DevState* __restrict__ st) {
-  if (st && st->done) return;   // uniform across the cluster: all blocks leave together
+                                           const float2* __restrict__ tw, const DevState* __restrict__ st,
+                                           BatchArgs ba) {
+  // blocks of one cluster share (instance, kx), so these exits are uniform
+  // across the cluster: all its blocks leave together
+  if (st && st->done) return;
+  const int inst = blockIdx.x / (g.hx * g.cly * g.clz);
+  if (ba.done && ba.done[(long long)inst * ba.done_stride]) return;
+  spec += (long long)inst * 3 * g.hx * g.nz * g.ny;
   extern __shared__ float2 s[];
   constexpr int RP = LY + 1;
   constexpr int PL = LY * LZ;   // points per component
@@ -190,7 +212,7 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
   const int ry = rank % g.cly, rz = rank / g.cly;
-  const int kx = blockIdx.x / CL;
+  const int kx = (blockIdx.x / CL) % g.hx;
   // 1. load and twiddle by exp(-2 pi i (y ry / py + z rz / pz))
 #pragma unroll 4
   for (int e = threadIdx.x; e < 3 * PL; e += NT) {
@@ -267,16 +289,16 @@ struct RowCfgT {
 };
 
 template <int L>
-void run_fx_t(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
+void run_fx_t(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
   using C = RowCfgT<L>;
-  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3);
-  k_fx_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, m, b.mask, b.region, b.lut, b.spec, b.tw, b.st);
+  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3 * ba.count);
+  k_fx_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, m, b.mask, b.region, b.lut, b.spec, b.tw, b.st, ba);
 }
 template <int L>
-void run_ix_t(const Geom& g, const Buffers& b, cudaStream_t s) {
+void run_ix_t(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
   using C = RowCfgT<L>;
-  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3);
-  k_ix_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, b.spec, b.bd, b.tw, b.st);
+  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3 * ba.count);
+  k_ix_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, b.spec, b.bd, b.tw, b.st, ba);
 }
 
 template <int LY, int LZ>
@@ -287,7 +309,7 @@ struct YzCfg {
 };
 
 template <int LY, int LZ>
-void run_yz(const Geom& g, const Buffers& b, cudaStream_t s) {
+void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
   using C = YzCfg<LY, LZ>;
   auto kern = k_yz<LY, LZ, C::NT>;
   static bool attr_set = false;
@@ -297,7 +319,7 @@ void run_yz(const Geom& g, const Buffers& b, cudaStream_t s) {
   }
   const int CL = g.cly * g.clz;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(g.hx * CL);
+  cfg.gridDim = dim3(g.hx * CL * ba.count);
   cfg.blockDim = dim3(C::NT);
   cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = s;
@@ -308,7 +330,7 @@ void run_yz(const Geom& g, const Buffers& b, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st);
+  cudaLaunchKernelEx(&cfg, kern, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st, ba);
 }
 
 __global__ void k_kt_transpose(Geom g, const float* __restrict__ kt, float* __restrict__ ktf) {
@@ -364,13 +386,17 @@ bool fused_plan(Geom& g) {
   }
 
 void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
-#define CALL_FX(LL) run_fx_t<LL>(g, b, m, s)
+  launch_demag_fused_batch(g, b, m, s, BatchArgs{1, nullptr, nullptr, 0});
+}
+
+void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
+#define CALL_FX(LL) run_fx_t<LL>(g, b, m, s, ba)
   MM_ROWL(g.lx, CALL_FX)
 #undef CALL_FX
   const int key = g.ly * 100 + g.lz;
   switch (key) {
 #define YZ(LY, LZ) \
-  case LY * 100 + LZ: run_yz<LY, LZ>(g, b, s); break;
+  case LY * 100 + LZ: run_yz<LY, LZ>(g, b, s, ba); break;
     YZ(16, 1) YZ(32, 1) YZ(64, 1) YZ(128, 1) YZ(256, 1) YZ(512, 1) YZ(1024, 1)
     YZ(16, 2) YZ(32, 2) YZ(64, 2) YZ(128, 2) YZ(256, 2) YZ(512, 2) YZ(1024, 2)
     YZ(16, 4) YZ(32, 4) YZ(64, 4) YZ(128, 4) YZ(256, 4) YZ(512, 4) YZ(1024, 4)
@@ -380,7 +406,7 @@ void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStr
 #undef YZ
     default: break;
   }
-#define CALL_IX(LL) run_ix_t<LL>(g, b, s)
+#define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
   MM_ROWL(g.lx, CALL_IX)
 #undef CALL_IX
 }

@@ -242,6 +242,31 @@ int eval_field(mm_ctx* c, int mode) {
 
 namespace mm {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+// Grid and padded-FFT geometry of an nx x ny x nz grid (the fused-path
+// fields are filled in by fused_plan).
+Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz) {
+  Geom g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.n = (long long)nx * ny * nz;
+  g.idx2 = (float)(1.0 / (dx * dx));
+  g.idy2 = (float)(1.0 / (dy * dy));
+  g.idz2 = (float)(1.0 / (dz * dz));
+  g.px = nx == 1 ? 1 : next_pow2(2 * nx - 1);
+  g.py = ny == 1 ? 1 : next_pow2(2 * ny - 1);
+  g.pz = nz == 1 ? 1 : next_pow2(2 * nz - 1);
+  g.lx = g.px == 1 ? 1 : g.px / 2;
+  g.hx = g.px == 1 ? 1 : g.lx + 1;
+  g.hxs = (g.hx + 7) / 8 * 8;
+  g.srows = g.pz > 1 ? g.py : ny;
+  g.sc = (long long)nz * g.srows * g.hxs;
+  g.hkx = g.px == 1 ? 1 : g.px / 2 + 1;
+  g.hky = g.py == 1 ? 1 : g.py / 2 + 1;
+  g.hkz = g.pz == 1 ? 1 : g.pz / 2 + 1;
+  return g;
+}
 }  // namespace mm
 
 extern "C" {
@@ -261,25 +286,8 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   c->dx = dx;
   c->dy = dy;
   c->dz = dz;
+  c->g = make_geom(nx, ny, nz, dx, dy, dz);
   Geom& g = c->g;
-  g.nx = nx;
-  g.ny = ny;
-  g.nz = nz;
-  g.n = (long long)nx * ny * nz;
-  g.idx2 = (float)(1.0 / (dx * dx));
-  g.idy2 = (float)(1.0 / (dy * dy));
-  g.idz2 = (float)(1.0 / (dz * dz));
-  g.px = nx == 1 ? 1 : next_pow2(2 * nx - 1);
-  g.py = ny == 1 ? 1 : next_pow2(2 * ny - 1);
-  g.pz = nz == 1 ? 1 : next_pow2(2 * nz - 1);
-  g.lx = g.px == 1 ? 1 : g.px / 2;
-  g.hx = g.px == 1 ? 1 : g.lx + 1;
-  g.hxs = (g.hx + 7) / 8 * 8;
-  g.srows = g.pz > 1 ? g.py : ny;
-  g.sc = (long long)nz * g.srows * g.hxs;
-  g.hkx = g.px == 1 ? 1 : g.px / 2 + 1;
-  g.hky = g.py == 1 ? 1 : g.py / 2 + 1;
-  g.hkz = g.pz == 1 ? 1 : g.pz / 2 + 1;
   fused_plan(g);
   for (int r = 0; r < kRegions; ++r) {
     std::memset(&c->mat[r], 0, sizeof(mm_material));

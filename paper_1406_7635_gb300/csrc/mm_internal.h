@@ -84,8 +84,23 @@ struct Buffers {
 
 struct Terms { int demag, exch, anis, zeeman; };
 
+Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz);
+
+// Instance dimension of the fused convolution kernels: `count` instances of
+// one grid laid out back to back; optional per-instance Msat (every cell
+// magnetic) and a per-instance done flag read at done[i * done_stride].
+struct BatchArgs {
+  int count;
+  const float* msat;
+  const int* done;
+  int done_stride;
+};
+
 // sets the message mm_last_error() returns on this thread
 void set_last_error(const std::string& msg);
+// grid and padded-FFT geometry (fused fields left zero; see fused_plan)
+struct Geom;
+
 
 // ---- launch wrappers (stream-ordered) ----
 // demag convolution of M = Msat m (m = `m`), result in b.bd
@@ -93,6 +108,7 @@ void launch_demag(const Geom& g, const Buffers& b, const float* m, cudaStream_t 
 // fused three-kernel convolution; fused_plan() decides whether g supports it
 bool fused_plan(Geom& g);
 void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
+void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba);
 void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s);
 // kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,

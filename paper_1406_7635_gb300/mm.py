@@ -45,6 +45,12 @@ class mm_stats(C.Structure):
                 ("last_err", C.c_double), ("t", C.c_double), ("dt", C.c_double), ("launches", C.c_longlong)]
 
 
+class mm_instance_spec(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dz", C.c_double), ("msat", C.c_double), ("aex", C.c_double), ("alpha", C.c_double),
+                ("gamma_ll", C.c_double), ("bext", C.c_double * 3)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -82,6 +88,15 @@ _SIGS = {
     "mm_demag_apply": (_I, [_P, _P, _P]),
     "mm_demag_field_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _P, _P, _P]),
     "mm_sync": (_I, [_P]),
+    "mm_batch_create": (_I, [C.POINTER(_P), _I, C.POINTER(mm_instance_spec), _I, _P]),
+    "mm_batch_destroy": (_I, [_P]),
+    "mm_batch_set_m": (_I, [_P, _I, _P]),
+    "mm_batch_get_m": (_I, [_P, _I, _P]),
+    "mm_batch_set_solver": (_I, [_P, _D, _D, _D, _D, _D]),
+    "mm_batch_run": (_I, [_P, _D]),
+    "mm_batch_get_stats": (_I, [_P, _I, C.POINTER(mm_stats)]),
+    "mm_batch_get_dt_history": (_I, [_P, _I, _P, _I, C.POINTER(_I)]),
+    "mm_batch_num_classes": (_I, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -280,3 +295,66 @@ class Context:
         ctx.set_solver(p.max_err, p.headroom, p.dt0, p.dt_min, p.dt_max)
         ctx.set_m(p.m0)
         return ctx
+
+
+class Batch:
+    """Independent simulations of uneven grids advanced together (mm_batch_*).
+
+    specs: sequence of dicts with nx, ny, nz, dx, dy, dz, msat, aex, alpha,
+    gamma_ll (optional), bext (3-vector)."""
+
+    def __init__(self, specs, device=0, stream=None):
+        arr = (mm_instance_spec * len(specs))()
+        self.shapes = []
+        for a, s in zip(arr, specs):
+            a.nx, a.ny, a.nz = s["nx"], s["ny"], s["nz"]
+            a.dx, a.dy, a.dz = s["dx"], s["dy"], s["dz"]
+            a.msat, a.aex, a.alpha = s["msat"], s["aex"], s["alpha"]
+            a.gamma_ll = s.get("gamma_ll", 1.7595e11)
+            a.bext = (C.c_double * 3)(*s["bext"])
+            self.shapes.append((s["nz"], s["ny"], s["nx"]))
+        h = C.c_void_p()
+        _check(mm_batch_create(C.byref(h), len(specs), arr, device, stream))
+        self.h = h
+        self.n = len(specs)
+
+    def close(self):
+        if self.h:
+            mm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_m(self, i, m):
+        a = np.ascontiguousarray(m, dtype=np.float32).reshape((3,) + self.shapes[i])
+        _check(mm_batch_set_m(self.h, i, _ptr(a)))
+
+    def get_m(self, i):
+        out = np.zeros((3,) + self.shapes[i], dtype=np.float32)
+        _check(mm_batch_get_m(self.h, i, _ptr(out)))
+        return out
+
+    def set_solver(self, max_err=1e-5, headroom=0.8, dt0=1e-14, dt_min=1e-20, dt_max=1e-10):
+        _check(mm_batch_set_solver(self.h, max_err, headroom, dt0, dt_min, dt_max))
+
+    def run(self, t_end):
+        _check(mm_batch_run(self.h, float(t_end)))
+
+    def get_stats(self, i):
+        s = mm_stats()
+        rc = mm_batch_get_stats(self.h, i, C.byref(s))
+        return {"accepted": s.accepted, "rejected": s.rejected, "evals": s.evals, "last_err": s.last_err,
+                "t": s.t, "dt": s.dt, "status": rc}
+
+    def get_dt_history(self, i, max_n=4096):
+        out = np.zeros(max_n, dtype=np.float64)
+        n = C.c_int()
+        _check(mm_batch_get_dt_history(self.h, i, _ptr(out), max_n, C.byref(n)))
+        return out[:n.value].copy()
+
+    def num_classes(self):
+        return mm_batch_num_classes(self.h)

@@ -191,3 +191,41 @@ WORKLOADS = {
     "grains_256x256x1": lambda: grain_film(256, 256, 64),
     "ellipsoid_128x128x32": lambda: ellipsoid_vortex(128, 128, 32),
 }
+
+
+# ---------------------------------------------------------------------------
+# Batched workload: many independent instances of uneven sizes.
+# ---------------------------------------------------------------------------
+BATCH_SHAPES = ((32, 32, 1), (64, 32, 1), (128, 64, 2), (96, 96, 4))
+
+
+def batch_instances(n=512, shapes=BATCH_SHAPES, cell=4e-9, seed=SEED_BASE + 3):
+    """n instance descriptions: grid drawn uniformly from `shapes` (nx, ny,
+    nz) with cubic cells; Msat ~ U[4e5, 1.2e6] A/m, Aex ~ U[0.8, 2]e-11 J/m,
+    alpha ~ U[0.005, 0.5]; a static field of uniform direction and magnitude
+    ~ U[0, 50] mT; m0 uniform on the unit sphere per cell.  Returns (specs,
+    m0s): dicts for the batched API and float64 arrays (3, nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    specs, m0s = [], []
+    for _ in range(n):
+        nx, ny, nz = shapes[rng.integers(len(shapes))]
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        spec = {"nx": int(nx), "ny": int(ny), "nz": int(nz), "dx": cell, "dy": cell, "dz": cell,
+                "msat": float(rng.uniform(4e5, 1.2e6)), "aex": float(rng.uniform(0.8e-11, 2e-11)),
+                "alpha": float(rng.uniform(0.005, 0.5)), "gamma_ll": GAMMA_LL,
+                "bext": (d * rng.uniform(0.0, 50e-3)).tolist()}
+        specs.append(spec)
+        m0s.append(random_unit(rng, (nz, ny, nx)))
+    return specs, m0s
+
+
+def problem_from_instance(spec, m0):
+    """The single-grid Problem equivalent to one batched instance."""
+    p = Problem(spec["nx"], spec["ny"], spec["nz"], spec["dx"], spec["dy"], spec["dz"])
+    p.msat[0], p.aex[0], p.alpha[0] = spec["msat"], spec["aex"], spec["alpha"]
+    p.gamma[0] = spec.get("gamma_ll", GAMMA_LL)
+    p.b0[0] = spec["bext"]
+    p.anis = False
+    p.m0 = np.asarray(m0, dtype=np.float64)
+    return p

@@ -1,0 +1,91 @@
+"""Batched multi-instance RK45 (many independent grids in one graph launch):
+each instance against the float64 oracle replaying that instance's own step
+sizes, and against the single-instance CUDA path."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.rk45 import RK45  # noqa: E402
+from paper_1406_7635_gb300.workloads import batch_instances, problem_from_instance  # noqa: E402
+
+M_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1406_7635_gb300.build import build
+    build()
+    from paper_1406_7635_gb300 import mm as _mm
+    return _mm
+
+
+SMALL_SHAPES = ((32, 32, 1), (64, 32, 1), (48, 24, 3), (17, 20, 2))
+
+
+@pytest.fixture(scope="module")
+def batch_run(mm):
+    specs, m0s = batch_instances(16, shapes=SMALL_SHAPES, seed=77)
+    b = mm.Batch(specs)
+    assert b.num_classes() == len({(s["nx"], s["ny"], s["nz"]) for s in specs})
+    for i, m in enumerate(m0s):
+        b.set_m(i, m)
+    t_end = 4e-12
+    b.run(t_end)
+    out = {"specs": specs, "m0s": m0s, "t_end": t_end,
+           "m": [b.get_m(i) for i in range(len(specs))],
+           "dts": [b.get_dt_history(i) for i in range(len(specs))],
+           "stats": [b.get_stats(i) for i in range(len(specs))]}
+    b.close()
+    return out
+
+
+def test_every_instance_reaches_t_end(batch_run):
+    for st in batch_run["stats"]:
+        assert st["status"] == 0
+        assert st["t"] == batch_run["t_end"]
+        assert st["accepted"] >= 1
+    # instances take different numbers of steps (their own adaptive dt)
+    assert len({st["accepted"] for st in batch_run["stats"]}) > 1
+
+
+@pytest.mark.parametrize("i", range(0, 16, 3))
+def test_instance_vs_oracle_replay(batch_run, i):
+    spec, m0 = batch_run["specs"][i], batch_run["m0s"][i]
+    p = problem_from_instance(spec, m0)
+    ora = RK45(p, m=p.m0.astype(np.float32).astype(np.float64))
+    ora.run_fixed(batch_run["dts"][i])
+    assert abs(ora.t - batch_run["t_end"]) <= 1e-9 * batch_run["t_end"]
+    assert np.abs(batch_run["m"][i].astype(np.float64) - ora.m).max() <= M_TOL
+
+
+@pytest.mark.parametrize("i", [0, 5, 10])
+def test_instance_vs_single_context(mm, batch_run, i):
+    spec, m0 = batch_run["specs"][i], batch_run["m0s"][i]
+    p = problem_from_instance(spec, m0)
+    ctx = mm.Context.from_problem(p)
+    ctx.set_fixed_dt_sequence(batch_run["dts"][i])
+    ctx.step(len(batch_run["dts"][i]))
+    m = ctx.get_m()
+    ctx.close()
+    # two float32 paths that round in different orders
+    assert np.abs(m.astype(np.float64) - batch_run["m"][i].astype(np.float64)).max() <= 5e-6
+
+
+def test_batch_nonfinite_instance_reports_error(mm):
+    specs, m0s = batch_instances(3, shapes=((32, 32, 1),), seed=5)
+    b = mm.Batch(specs)
+    for i, m in enumerate(m0s):
+        mm_ = m.copy()
+        if i == 1:
+            mm_[0, 0, 3, 3] = np.nan
+        b.set_m(i, mm_)
+    with pytest.raises(mm.MMError) as ei:
+        b.run(1e-12)
+    assert ei.value.code == -4
+    assert b.get_stats(1)["status"] == -4
+    assert b.get_stats(0)["status"] == 0
+    b.close()
