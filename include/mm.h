@@ -194,6 +194,54 @@ int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double dy, double 
 /* Blocks until the context's stream is idle. */
 int mm_sync(mm_ctx* ctx);
 
+/* ---- Learned demag surrogate ----------------------------------------------
+ * A Fourier-neural-operator approximation of the demag field of a 2-D film
+ * (the learned form of the convolution of Sec. III.B; the paper has none).
+ * u = Msat m / ms_ref -> y = B_demag / (mu0 ms_ref):
+ *   v_0 = P u + p;  v_{l+1} = act(W_l v_l + b_l + K_l v_l);  y = Q v_L + q,
+ * act = GELU (none after the last layer), K_l the spectral convolution
+ * truncated to kx < modes_x and ky in {0..modes_y-1} U {H-modes_y..H-1},
+ * written with explicit partial DFTs (Re of the inverse).  Dense products run
+ * on the bfloat16 tensor cores with float32 accumulation; parameters are
+ * float32 (Adam), flat in the order P, p, {W_l, b_l, R_l}, Q, q with R_l
+ * complex [width][width][2 modes_y][modes_x] as (re, im) pairs.
+ * Loss: sum |yhat - y|^2 / sum |y|^2 over a batch. */
+typedef struct mm_fno mm_fno;
+typedef struct {
+  int width, layers, modes_x, modes_y;
+  int max_batch;               /* samples per forward/backward call        */
+  unsigned long long seed;     /* initial parameters                       */
+} mm_fno_cfg;
+int mm_fno_create(mm_fno** out, int ny, int nx, const mm_fno_cfg* cfg, int device, void* cuda_stream);
+int mm_fno_destroy(mm_fno* f);
+long long mm_fno_param_count(mm_fno* f);
+int mm_fno_get_params(mm_fno* f, float* host, long long n);
+int mm_fno_set_params(mm_fno* f, const float* host, long long n);   /* resets Adam */
+/* Device pointers, float32 [S][3][ny][nx]. */
+int mm_fno_forward(mm_fno* f, const float* u, float* y, int S);
+/* Loss and its gradient (host array of param_count floats, may be NULL). */
+int mm_fno_grad(mm_fno* f, const float* u, const float* y, int S, float* grad_host, double* loss);
+/* One Adam step (beta 0.9, 0.999) on the batch; returns the batch loss. */
+int mm_fno_train_step(mm_fno* f, const float* u, const float* y, int S, double lr, double* loss);
+/* Trains `net` on n_pairs (m, B_demag) pairs taken from the context's own
+ * exact trajectories: traj_len pairs per trajectory, steps_between exact RK45
+ * steps apart, each trajectory from m uniform on the sphere per cell under a
+ * static field of uniform direction and magnitude U[0, field_max]; then
+ * `epochs` passes of Adam over shuffled batches.  The context's m, time and
+ * fields are restored.  *final_loss receives the last batch loss. */
+int mm_surrogate_train(mm_ctx* ctx, mm_fno* net, double ms_ref, int n_pairs, int traj_len,
+                       int steps_between, double field_max, int epochs, int batch, double lr,
+                       unsigned long long seed, double* final_loss);
+/* Uses `net` for the demag field inside every RK stage (net NULL: exact
+ * convolution).  Every check_every accepted steps the exact convolution
+ * judges the surrogate at the current m; once the relative L2 field error
+ * exceeds fallback_rel_err the context returns to the exact path for good.
+ * Only mm_step is available in this mode. */
+int mm_set_demag_surrogate(mm_ctx* ctx, mm_fno* net, double ms_ref, int check_every,
+                           double fallback_rel_err);
+int mm_get_surrogate_stats(mm_ctx* ctx, long long* steps_with_surrogate, long long* checks,
+                           long long* fallbacks, double* last_rel_err, int* active);
+
 /* ---- Batched simulations --------------------------------------------------
  * Many independent simulations of uneven grid sizes advanced together, each
  * with its own adaptive Dormand-Prince step (Sec. IV) and its own material and

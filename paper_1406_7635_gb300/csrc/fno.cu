@@ -1,0 +1,723 @@
+// Fourier-neural-operator surrogate of the demag field: forward, backward and
+// Adam on the GPU (the learned form of the demag convolution of Sec. III.B).
+//
+//   v_0 = P u + p,  v_{l+1} = act_l(W_l v_l + b_l + K_l v_l),  y = Q v_L + q
+//
+// u = M / Ms_ref (3 channels on an H x W film), y = B_demag / (mu0 Ms_ref).
+// K_l is the truncated spectral convolution written with explicit partial DFT
+// matrices (kx < Mx; ky in {0..My-1} U {H-My..H-1}):
+//   V = Fy v Fx^T,  O[o] = sum_i R[o,i] V[i] (per mode),  K v = Re(Gy^T O Gx),
+// Gx = c_kx exp(+2 pi i kx x / W) / W (c_0 = 1, else 2), Gy = exp(+...)/H.
+// act = exact GELU except after the last layer.  Loss: sum |yhat - y|^2 /
+// sum |y|^2 over the batch.
+//
+// Activations are float32, channel-major [C][H][W].  The dense products (lift,
+// project, pointwise W, the x-direction partial DFTs and their adjoints) run
+// on the tensor cores: operands rounded to bfloat16 while staged in shared
+// memory, float32 accumulation (mma m16n8k16).  The y-direction partial DFTs
+// and the per-mode channel mixing are small complex products on the FP32
+// cores.  Parameters are float32 masters (Adam), used in bfloat16 by the
+// tensor-core products.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "../../include/mm.h"
+#include "mm_internal.h"
+
+namespace mm {
+namespace {
+
+// ---------------------------------------------------------------------------
+// bfloat16 tensor-core GEMM: C[b] = alpha op(A[b]) op(B[b]) + beta C[b]
+// (+ bias[m]).  op(A)(m, k) = TA ? A[k lda + m] : A[m lda + k];
+// op(B)(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  Split-K (gridDim.z =
+// batch * splits) adds alpha * partial into C with atomics (C prepared by the
+// caller).  Block tile 64 x 64 x 32, four warps of 32 x 32.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  int M, N, K;
+  const float* A;
+  long long lda, sA;   // leading dimension, batch stride
+  const float* B;
+  long long ldb, sB;
+  float* C;
+  long long ldc, sC;
+  float alpha, beta;
+  const float* bias;   // per-row bias or null
+  int splits;          // split-K factor
+  int atomic;          // add alpha * product into C with atomics (C prepared by the caller)
+};
+
+constexpr int BM = 64, BN = 64, BK = 32, APITCH = BK + 8;
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
+  __shared__ __align__(16) __nv_bfloat16 As[BM][APITCH];
+  __shared__ __align__(16) __nv_bfloat16 Bs[BN][APITCH];
+  const int batch = blockIdx.z / a.splits, split = blockIdx.z % a.splits;
+  const float* __restrict__ A = a.A + batch * a.sA;
+  const float* __restrict__ B = a.B + batch * a.sB;
+  float* __restrict__ Cm = a.C + batch * a.sC;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kchunk = ((a.K + a.splits - 1) / a.splits + BK - 1) / BK * BK;
+  const int kbeg = split * kchunk, kend = min(a.K, kbeg + kchunk);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    // stage A (BM x BK) and B (BN x BK), k contiguous in shared memory
+#pragma unroll 4
+    for (int e = tid; e < BM * BK / 2; e += 128) {
+      int mm_, kk;
+      if (TA) { mm_ = (2 * e) % BM; kk = (2 * e) / BM; } else { mm_ = (2 * e) / BK; kk = (2 * e) % BK; }
+      float v0 = 0.f, v1 = 0.f;
+      if (TA) {
+        const int gm = m0 + mm_, gk = k0 + kk;
+        if (gk < kend) {
+          if (gm < a.M) v0 = A[(long long)gk * a.lda + gm];
+          if (gm + 1 < a.M) v1 = A[(long long)gk * a.lda + gm + 1];
+        }
+        As[mm_][kk] = __float2bfloat16_rn(v0);
+        As[mm_ + 1][kk] = __float2bfloat16_rn(v1);
+      } else {
+        const int gm = m0 + mm_, gk = k0 + kk;
+        if (gm < a.M) {
+          if (gk < kend) v0 = A[(long long)gm * a.lda + gk];
+          if (gk + 1 < kend) v1 = A[(long long)gm * a.lda + gk + 1];
+        }
+        *reinterpret_cast<unsigned*>(&As[mm_][kk]) = pack_bf16(v0, v1);
+      }
+    }
+#pragma unroll 4
+    for (int e = tid; e < BN * BK / 2; e += 128) {
+      int nn, kk;
+      if (TB) { nn = (2 * e) / BK; kk = (2 * e) % BK; } else { nn = (2 * e) % BN; kk = (2 * e) / BN; }
+      float v0 = 0.f, v1 = 0.f;
+      if (TB) {
+        const int gn = n0 + nn, gk = k0 + kk;
+        if (gn < a.N) {
+          if (gk < kend) v0 = B[(long long)gn * a.ldb + gk];
+          if (gk + 1 < kend) v1 = B[(long long)gn * a.ldb + gk + 1];
+        }
+        *reinterpret_cast<unsigned*>(&Bs[nn][kk]) = pack_bf16(v0, v1);
+      } else {
+        const int gn = n0 + nn, gk = k0 + kk;
+        if (gk < kend) {
+          if (gn < a.N) v0 = B[(long long)gk * a.ldb + gn];
+          if (gn + 1 < a.N) v1 = B[(long long)gk * a.ldb + gn + 1];
+        }
+        Bs[nn][kk] = __float2bfloat16_rn(v0);
+        Bs[nn + 1][kk] = __float2bfloat16_rn(v1);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      unsigned af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g;
+        af[i][0] = *reinterpret_cast<const unsigned*>(&As[r][ks + 2 * t]);
+        af[i][1] = *reinterpret_cast<const unsigned*>(&As[r + 8][ks + 2 * t]);
+        af[i][2] = *reinterpret_cast<const unsigned*>(&As[r][ks + 2 * t + 8]);
+        af[i][3] = *reinterpret_cast<const unsigned*>(&As[r + 8][ks + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + g;
+        bfr[j][0] = *reinterpret_cast<const unsigned*>(&Bs[c][ks + 2 * t]);
+        bfr[j][1] = *reinterpret_cast<const unsigned*>(&Bs[c][ks + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+              "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+    }
+    __syncthreads();
+  }
+  // epilogue
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
+        const int col = n0 + wn + 8 * j + 2 * t + (r & 1);
+        if (row >= a.M || col >= a.N) continue;
+        float* dst = Cm + (long long)row * a.ldc + col;
+        const float v = a.alpha * acc[i][j][r];
+        if (a.atomic) {
+          atomicAdd(dst, v);
+        } else {
+          float out = v + (a.bias ? a.bias[row] : 0.f);
+          if (a.beta != 0.f) out += a.beta * *dst;
+          *dst = out;
+        }
+      }
+}
+
+void gemm(cudaStream_t s, bool ta, bool tb, int batch, const GemmArgs& a) {
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, batch * a.splits);
+  if (!ta && !tb) k_gemm<false, false><<<grid, 128, 0, s>>>(a);
+  else if (ta && !tb) k_gemm<true, false><<<grid, 128, 0, s>>>(a);
+  else if (!ta && tb) k_gemm<false, true><<<grid, 128, 0, s>>>(a);
+  else k_gemm<true, true><<<grid, 128, 0, s>>>(a);
+}
+
+GemmArgs gargs(int M, int N, int K, const float* A, long long lda, long long sA, const float* B, long long ldb,
+               long long sB, float* C, long long ldc, long long sC, float alpha = 1.f, float beta = 0.f,
+               const float* bias = nullptr, int splits = 1, int atomic = 0) {
+  return GemmArgs{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, beta, bias, splits, atomic || splits > 1};
+}
+
+// ---------------------------------------------------------------------------
+// small complex kernels (FP32 cores)
+// ---------------------------------------------------------------------------
+// Y[c][j][k] = sum_y F[j][y] * X[c][y][k]; X blocked real [c][y][re Mx | im Mx]
+// (if xin_blocked) or complex [c][y][k]; conj_f conjugates F.  Output complex.
+__global__ void k_ysum(int S, int C, int H, int J, int Mx, const float* __restrict__ X, bool x_blocked,
+                       const float2* __restrict__ F, bool conj_f, float2* __restrict__ Y) {
+  const long long total = (long long)S * C * J * Mx;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = (int)(i % Mx), j = (int)((i / Mx) % J);
+  const long long sc = i / ((long long)Mx * J);   // sample * C + c
+  float re = 0.f, im = 0.f;
+  for (int y = 0; y < H; ++y) {
+    float2 f = F[(long long)j * H + y];
+    if (conj_f) f.y = -f.y;
+    float xr, xi;
+    if (x_blocked) {
+      const float* row = X + (sc * H + y) * 2 * Mx;
+      xr = row[k];
+      xi = row[Mx + k];
+    } else {
+      const float2 v = reinterpret_cast<const float2*>(X)[(sc * H + y) * Mx + k];
+      xr = v.x;
+      xi = v.y;
+    }
+    re = fmaf(f.x, xr, fmaf(-f.y, xi, re));
+    im = fmaf(f.x, xi, fmaf(f.y, xr, im));
+  }
+  Y[i] = make_float2(re, im);
+}
+
+// Z[c][y][re k | im k] = sum_j F[j][y] * O[c][j][k] (conj_f: conj(F)), blocked real output
+__global__ void k_yexpand(int S, int C, int H, int J, int Mx, const float2* __restrict__ O,
+                          const float2* __restrict__ F, bool conj_f, float* __restrict__ Z) {
+  const long long total = (long long)S * C * H * Mx;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = (int)(i % Mx), y = (int)((i / Mx) % H);
+  const long long sc = i / ((long long)Mx * H);
+  float re = 0.f, im = 0.f;
+  for (int j = 0; j < J; ++j) {
+    float2 f = F[(long long)j * H + y];
+    if (conj_f) f.y = -f.y;
+    const float2 o = O[(sc * J + j) * Mx + k];
+    re = fmaf(f.x, o.x, fmaf(-f.y, o.y, re));
+    im = fmaf(f.x, o.y, fmaf(f.y, o.x, im));
+  }
+  float* row = Z + (sc * H + y) * 2 * Mx;
+  row[k] = re;
+  row[Mx + k] = im;
+}
+
+// O[s][o][m] = sum_i R[o][i][m] V[s][i][m]   (conj: sum_o conj(R[o][i][m]) V[s][o][m] -> O[s][i][m])
+__global__ void k_mix(int S, int C, int NM, const float2* __restrict__ R, const float2* __restrict__ V,
+                      float2* __restrict__ O, bool adjoint) {
+  const long long total = (long long)S * C * NM;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int m = (int)(idx % NM), o = (int)((idx / NM) % C);
+  const long long s = idx / ((long long)NM * C);
+  float re = 0.f, im = 0.f;
+  for (int i = 0; i < C; ++i) {
+    float2 r = adjoint ? R[((long long)i * C + o) * NM + m] : R[((long long)o * C + i) * NM + m];
+    if (adjoint) r.y = -r.y;
+    const float2 v = V[(s * C + i) * NM + m];
+    re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
+    im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
+  }
+  O[idx] = make_float2(re, im);
+}
+
+// dR[o][i][m] += sum_s dO[s][o][m] conj(V[s][i][m])
+__global__ void k_dR(int S, int C, int NM, const float2* __restrict__ dO, const float2* __restrict__ V,
+                     float2* __restrict__ dR) {
+  const long long total = (long long)C * C * NM;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int m = (int)(idx % NM), i = (int)((idx / NM) % C), o = (int)(idx / ((long long)NM * C));
+  float re = 0.f, im = 0.f;
+  for (int s = 0; s < S; ++s) {
+    const float2 d = dO[((long long)s * C + o) * NM + m];
+    const float2 v = V[((long long)s * C + i) * NM + m];
+    re += d.x * v.x + d.y * v.y;
+    im += d.y * v.x - d.x * v.y;
+  }
+  dR[idx].x += re;
+  dR[idx].y += im;
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_df(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
+}
+
+__global__ void k_gelu(long long n, const float* __restrict__ z, float* __restrict__ v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = gelu_f(z[i]);
+}
+__global__ void k_gelu_back(long long n, const float* __restrict__ z, float* __restrict__ dv) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dv[i] *= gelu_df(z[i]);
+}
+
+// sum over pixels per (row) for bias gradients: out[r] += sum_{s,p} d[s][r][p]
+__global__ void k_rowsum(int S, int R, long long P, const float* __restrict__ d, float* __restrict__ out) {
+  const int r = blockIdx.x;
+  float acc = 0.f;
+  for (int s = 0; s < S; ++s)
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) acc += d[((long long)s * R + r) * P + p];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    out[r] += v;
+  }
+}
+
+// loss pieces: acc[0] += sum (yhat - y)^2, acc[1] += sum y^2
+__global__ void k_loss(long long n, const float* __restrict__ yh, const float* __restrict__ y, double* acc) {
+  double a = 0.0, b = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)yh[i] - (double)y[i];
+    a += d * d;
+    b += (double)y[i] * y[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], a);
+    atomicAdd(&acc[1], b);
+  }
+}
+
+__global__ void k_dloss(long long n, const float* __restrict__ yh, const float* __restrict__ y,
+                        const double* __restrict__ acc, float* __restrict__ dy) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dy[i] = (float)(2.0 * ((double)yh[i] - (double)y[i]) / acc[1]);
+}
+
+__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
+                       float* __restrict__ m2, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = gr[i];
+  const float a = b1 * m1[i] + (1.f - b1) * g;
+  const float b = b2 * m2[i] + (1.f - b2) * g * g;
+  m1[i] = a;
+  m2[i] = b;
+  p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+// u = (Msat(cell) / ms_ref) m  and  B = mu0 ms_ref y
+__global__ void k_to_u(long long n, const float* __restrict__ m, const uint8_t* __restrict__ mask,
+                       const uint8_t* __restrict__ region, const RegionLUT* __restrict__ lut, float inv_ref,
+                       float* __restrict__ u) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float s = mask[i] ? lut->msat[region[i]] * inv_ref : 0.f;
+  u[i] = s * m[i];
+  u[n + i] = s * m[n + i];
+  u[2 * n + i] = s * m[2 * n + i];
+}
+
+__global__ void k_scale(long long n, const float* __restrict__ x, float s, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = s * x[i];
+}
+
+__global__ void k_rel_err(long long n, const float* __restrict__ a, const float* __restrict__ b, double* acc) {
+  double x = 0.0, y = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)a[i] - (double)b[i];
+    x += d * d;
+    y += (double)b[i] * b[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], x);
+    atomicAdd(&acc[1], y);
+  }
+}
+
+unsigned nb(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace mm
+
+using namespace mm;
+
+struct mm_fno {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int C = 0, L = 0, Mx = 0, My = 0, H = 0, W = 0, J = 0, Smax = 0;
+  long long N = 0, nparam = 0;
+  std::vector<long long> off;   // P, p, {W, b, R} per layer, Q, q
+  float *prm = nullptr, *grd = nullptr, *m1 = nullptr, *m2 = nullptr;
+  long long adam_t = 0;
+  // constant partial-DFT matrices
+  float *Fblk = nullptr, *Gblk = nullptr;   // [W][2Mx], [2Mx][W]
+  float2 *Fy = nullptr, *Gy = nullptr;      // [J][H]
+  // activations and caches for Smax samples
+  float *u = nullptr, *yh = nullptr, *dy = nullptr;
+  std::vector<float*> v, z;                 // L+1 and L
+  std::vector<float2*> V;                   // L
+  float *X = nullptr, *Z = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr;
+  float2 *O = nullptr, *dO = nullptr, *dV = nullptr;
+  double* acc = nullptr;
+};
+
+namespace {
+
+int ffail(int code, const std::string& msg) {
+  mm::set_last_error(msg);
+  return code;
+}
+
+#define MMF_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return ffail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,                \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+float* P_(mm_fno* f, int k) { return f->prm + f->off[k]; }
+float* G_(mm_fno* f, int k) { return f->grd + f->off[k]; }
+// parameter slots: 0 P, 1 p, 2 + 3l W_l, 3 + 3l b_l, 4 + 3l R_l, 2 + 3L Q, 3 + 3L q
+int sW(int l) { return 2 + 3 * l; }
+int sb(int l) { return 3 + 3 * l; }
+int sR(int l) { return 4 + 3 * l; }
+
+// forward for S samples whose inputs are already in f->u; output in f->yh
+void fwd(mm_fno* f, int S) {
+  cudaStream_t s = f->stream;
+  const int C = f->C, H = f->H, W = f->W, Mx = f->Mx, J = f->J;
+  const long long N = f->N, CN = (long long)C * N;
+  const int L = f->L;
+  const int q = sW(L) , qq = sb(L);
+  // lift: v0[C x N] = P[C x 3] u[3 x N] + p
+  gemm(s, false, false, S, gargs(C, (int)N, 3, P_(f, 0), 3, 0, f->u, N, 3 * N, f->v[0], N, CN, 1.f, 0.f, P_(f, 1)));
+  for (int l = 0; l < L; ++l) {
+    float* vin = f->v[l];
+    // X = v [C H x W] . Fblk [W x 2Mx]
+    gemm(s, false, false, S, gargs(C * H, 2 * Mx, W, vin, W, CN, f->Fblk, 2 * Mx, 0, f->X, 2 * Mx,
+                                   (long long)C * H * 2 * Mx));
+    k_ysum<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->X, true, f->Fy, false, f->V[l]);
+    k_mix<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
+                                                      f->V[l], f->O, false);
+    k_yexpand<<<nb((long long)S * C * H * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->O, f->Gy, false, f->Z);
+    // z = Z_blk [C H x 2Mx] . Gblk [2Mx x W]  (spectral part), then += W v + b
+    gemm(s, false, false, S, gargs(C * H, W, 2 * Mx, f->Z, 2 * Mx, (long long)C * H * 2 * Mx, f->Gblk, W, 0, f->z[l],
+                                   W, CN));
+    gemm(s, false, false, S, gargs(C, (int)N, C, P_(f, sW(l)), C, 0, vin, N, CN, f->z[l], N, CN, 1.f, 1.f,
+                                   P_(f, sb(l))));
+    if (l < L - 1) k_gelu<<<nb(S * CN), 256, 0, s>>>(S * CN, f->z[l], f->v[l + 1]);
+    else cudaMemcpyAsync(f->v[l + 1], f->z[l], S * CN * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  }
+  // project: y[3 x N] = Q[3 x C] v_L + q
+  gemm(s, false, false, S, gargs(3, (int)N, C, P_(f, q), C, 0, f->v[L], N, CN, f->yh, N, 3 * N, 1.f, 0.f, P_(f, qq)));
+}
+
+// gradients of the batch loss into f->grd (zeroed here); loss pieces in acc
+void bwd(mm_fno* f, int S, const float* y) {
+  cudaStream_t s = f->stream;
+  const int C = f->C, H = f->H, W = f->W, Mx = f->Mx, J = f->J, L = f->L;
+  const long long N = f->N, CN = (long long)C * N;
+  const int splits = (int)std::min<long long>(64, std::max<long long>(1, N / 4096));
+  cudaMemsetAsync(f->grd, 0, f->nparam * sizeof(float), s);
+  cudaMemsetAsync(f->acc, 0, 2 * sizeof(double), s);
+  k_loss<<<1024, 256, 0, s>>>(S * 3 * N, f->yh, y, f->acc);
+  k_dloss<<<nb(S * 3 * N), 256, 0, s>>>(S * 3 * N, f->yh, y, f->acc, f->dy);
+  // project
+  for (int b = 0; b < S; ++b)
+    gemm(s, false, true, 1, gargs(3, C, (int)N, f->dy + b * 3 * N, N, 0, f->v[L] + b * CN, N, 0, G_(f, sW(L)), C, 0,
+                                  1.f, 0.f, nullptr, splits, 1));
+  k_rowsum<<<3, 256, 0, s>>>(S, 3, N, f->dy, G_(f, sb(L)));
+  gemm(s, true, false, S, gargs(C, (int)N, 3, P_(f, sW(L)), C, 0, f->dy, N, 3 * N, f->dv, N, CN));
+  for (int l = L - 1; l >= 0; --l) {
+    if (l < L - 1) k_gelu_back<<<nb(S * CN), 256, 0, s>>>(S * CN, f->z[l], f->dv);
+    float* dzl = f->dv;   // dz
+    for (int b = 0; b < S; ++b)
+      gemm(s, false, true, 1, gargs(C, C, (int)N, dzl + b * CN, N, 0, f->v[l] + b * CN, N, 0, G_(f, sW(l)), C, 0, 1.f,
+                                    0.f, nullptr, splits, 1));
+    k_rowsum<<<C, 256, 0, s>>>(S, C, N, dzl, G_(f, sb(l)));
+    // dv2 = W^T dz
+    gemm(s, true, false, S, gargs(C, (int)N, C, P_(f, sW(l)), C, 0, dzl, N, CN, f->dv2, N, CN));
+    // spectral adjoint: dZ_blk = dz [C H x W] . Gblk^T
+    gemm(s, false, true, S, gargs(C * H, 2 * Mx, W, dzl, W, CN, f->Gblk, W, 0, f->Z, 2 * Mx, (long long)C * H * 2 * Mx));
+    k_ysum<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->Z, true, f->Gy, true, f->dO);
+    k_dR<<<nb((long long)C * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, f->dO, f->V[l],
+                                                      reinterpret_cast<float2*>(G_(f, sR(l))));
+    k_mix<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
+                                                      f->dO, f->dV, true);
+    k_yexpand<<<nb((long long)S * C * H * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->dV, f->Fy, true, f->X);
+    // dv2 += dX_blk [C H x 2Mx] . Fblk^T [2Mx x W]
+    gemm(s, false, true, S, gargs(C * H, W, 2 * Mx, f->X, 2 * Mx, (long long)C * H * 2 * Mx, f->Fblk, 2 * Mx, 0, f->dv2,
+                                  W, CN, 1.f, 1.f));
+    std::swap(f->dv, f->dv2);
+  }
+  // lift
+  for (int b = 0; b < S; ++b)
+    gemm(s, false, true, 1, gargs(C, 3, (int)N, f->dv + b * CN, N, 0, f->u + b * 3 * N, N, 0, G_(f, 0), 3, 0, 1.f, 0.f,
+                                  nullptr, splits, 1));
+  k_rowsum<<<C, 256, 0, s>>>(S, C, N, f->dv, G_(f, 1));
+}
+
+}  // namespace
+
+extern "C" {
+
+int mm_fno_create(mm_fno** out, int H, int W, const mm_fno_cfg* cfg, int device, void* stream) {
+  if (!out || !cfg) return ffail(MM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const int C = cfg->width, L = cfg->layers, Mx = cfg->modes_x, My = cfg->modes_y, Smax = cfg->max_batch;
+  if (H < 2 || W < 2 || C < 1 || L < 1 || Mx < 1 || My < 1 || Smax < 1 || Mx > W / 2 || 2 * My > H)
+    return ffail(MM_ERR_ARG, "need H, W >= 2, width, layers, batch >= 1, modes_x <= W/2, 2 modes_y <= H");
+  MMF_CUDA(cudaSetDevice(device));
+  mm_fno* f = new mm_fno();
+  f->device = device;
+  f->C = C; f->L = L; f->Mx = Mx; f->My = My; f->H = H; f->W = W; f->J = 2 * My; f->Smax = Smax;
+  f->N = (long long)H * W;
+  auto cleanup = [&](int code) { mm_fno_destroy(f); return code; };
+  // parameter layout
+  long long o = 0;
+  auto add = [&](long long n) { f->off.push_back(o); o += n; };
+  add((long long)C * 3);
+  add(C);
+  for (int l = 0; l < L; ++l) {
+    add((long long)C * C);
+    add(C);
+    add(2LL * C * C * f->J * Mx);
+  }
+  add(3LL * C);
+  add(3);
+  f->nparam = o;
+  cudaError_t e = cudaSuccess;
+  if (stream) f->stream = (cudaStream_t)stream;
+  else { e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking); f->own_stream = e == cudaSuccess; }
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, f->stream);
+  };
+  alloc((void**)&f->prm, o * sizeof(float));
+  alloc((void**)&f->grd, o * sizeof(float));
+  alloc((void**)&f->m1, o * sizeof(float));
+  alloc((void**)&f->m2, o * sizeof(float));
+  alloc((void**)&f->Fblk, (size_t)W * 2 * Mx * sizeof(float));
+  alloc((void**)&f->Gblk, (size_t)2 * Mx * W * sizeof(float));
+  alloc((void**)&f->Fy, (size_t)f->J * H * sizeof(float2));
+  alloc((void**)&f->Gy, (size_t)f->J * H * sizeof(float2));
+  const long long CN = (long long)C * f->N;
+  alloc((void**)&f->u, (size_t)Smax * 3 * f->N * sizeof(float));
+  alloc((void**)&f->yh, (size_t)Smax * 3 * f->N * sizeof(float));
+  alloc((void**)&f->dy, (size_t)Smax * 3 * f->N * sizeof(float));
+  f->v.assign(L + 1, nullptr);
+  f->z.assign(L, nullptr);
+  f->V.assign(L, nullptr);
+  for (int l = 0; l <= L; ++l) alloc((void**)&f->v[l], (size_t)Smax * CN * sizeof(float));
+  for (int l = 0; l < L; ++l) alloc((void**)&f->z[l], (size_t)Smax * CN * sizeof(float));
+  for (int l = 0; l < L; ++l) alloc((void**)&f->V[l], (size_t)Smax * C * f->J * Mx * sizeof(float2));
+  alloc((void**)&f->X, (size_t)Smax * C * H * 2 * Mx * sizeof(float));
+  alloc((void**)&f->Z, (size_t)Smax * C * H * 2 * Mx * sizeof(float));
+  alloc((void**)&f->dv, (size_t)Smax * CN * sizeof(float));
+  alloc((void**)&f->dv2, (size_t)Smax * CN * sizeof(float));
+  alloc((void**)&f->O, (size_t)Smax * C * f->J * Mx * sizeof(float2));
+  alloc((void**)&f->dO, (size_t)Smax * C * f->J * Mx * sizeof(float2));
+  alloc((void**)&f->dV, (size_t)Smax * C * f->J * Mx * sizeof(float2));
+  alloc((void**)&f->acc, 4 * sizeof(double));
+  if (e != cudaSuccess) return cleanup(ffail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, cudaGetErrorString(e)));
+  // partial DFT matrices (float64 on the host, rounded once)
+  const double pi = 3.14159265358979323846;
+  std::vector<float> Fb((size_t)W * 2 * Mx), Gb((size_t)2 * Mx * W);
+  for (int x = 0; x < W; ++x)
+    for (int k = 0; k < Mx; ++k) {
+      const double a = 2.0 * pi * (double)((long long)k * x % W) / W;
+      Fb[(size_t)x * 2 * Mx + k] = (float)std::cos(a);
+      Fb[(size_t)x * 2 * Mx + Mx + k] = (float)-std::sin(a);
+      const double c = (k == 0 ? 1.0 : 2.0) / W;
+      Gb[(size_t)k * W + x] = (float)(c * std::cos(a));           // Re(Z Gx) = Zr Gr - Zi Gi
+      Gb[(size_t)(Mx + k) * W + x] = (float)(-c * std::sin(a));
+    }
+  std::vector<float2> fy((size_t)f->J * H), gy((size_t)f->J * H);
+  for (int j = 0; j < f->J; ++j) {
+    const int ky = j < My ? j : H - 2 * My + j;
+    for (int y = 0; y < H; ++y) {
+      const double a = 2.0 * pi * (double)((long long)ky * y % H) / H;
+      fy[(size_t)j * H + y] = make_float2((float)std::cos(a), (float)-std::sin(a));
+      gy[(size_t)j * H + y] = make_float2((float)(std::cos(a) / H), (float)(std::sin(a) / H));
+    }
+  }
+  e = cudaMemcpyAsync(f->Fblk, Fb.data(), Fb.size() * sizeof(float), cudaMemcpyHostToDevice, f->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->Gblk, Gb.data(), Gb.size() * sizeof(float), cudaMemcpyHostToDevice, f->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->Fy, fy.data(), fy.size() * sizeof(float2), cudaMemcpyHostToDevice, f->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->Gy, gy.data(), gy.size() * sizeof(float2), cudaMemcpyHostToDevice, f->stream);
+  // initial parameters: scaled normal draws from a seeded generator
+  std::vector<float> p0(o, 0.0f);
+  unsigned long long st = cfg->seed * 0x9E3779B97F4A7C15ULL + 1;
+  auto unif = [&]() {   // splitmix64 -> (0, 1)
+    st += 0x9E3779B97F4A7C15ULL;
+    unsigned long long z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  auto normal = [&]() { return std::sqrt(-2.0 * std::log(unif())) * std::cos(2.0 * pi * unif()); };
+  auto fill = [&](int slot, long long n, double scale) {
+    for (long long i = 0; i < n; ++i) p0[f->off[slot] + i] = (float)(scale * normal());
+  };
+  fill(0, 3LL * C, 1.0 / std::sqrt(3.0));
+  for (int l = 0; l < L; ++l) {
+    fill(sW(l), (long long)C * C, 1.0 / std::sqrt((double)C));
+    fill(sR(l), 2LL * C * C * f->J * Mx, 1.0 / C);
+  }
+  fill(sW(L), 3LL * C, 1.0 / std::sqrt((double)C));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->prm, p0.data(), o * sizeof(float), cudaMemcpyHostToDevice, f->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return cleanup(ffail(MM_ERR_CUDA, cudaGetErrorString(e)));
+  *out = f;
+  return MM_OK;
+}
+
+int mm_fno_destroy(mm_fno* f) {
+  if (!f) return MM_OK;
+  cudaSetDevice(f->device);
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  void* ptrs[] = {f->prm, f->grd, f->m1, f->m2, f->Fblk, f->Gblk, f->Fy, f->Gy, f->u, f->yh, f->dy,
+                  f->X, f->Z, f->dv, f->dv2, f->O, f->dO, f->dV, f->acc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (float* p : f->v) if (p) cudaFree(p);
+  for (float* p : f->z) if (p) cudaFree(p);
+  for (float2* p : f->V) if (p) cudaFree(p);
+  if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
+  delete f;
+  return MM_OK;
+}
+
+long long mm_fno_param_count(mm_fno* f) { return f ? f->nparam : 0; }
+
+int mm_fno_get_params(mm_fno* f, float* host, long long n) {
+  if (!f || !host || n != f->nparam) return ffail(MM_ERR_ARG, "bad arguments");
+  MMF_CUDA(cudaMemcpyAsync(host, f->prm, n * sizeof(float), cudaMemcpyDeviceToHost, f->stream));
+  MMF_CUDA(cudaStreamSynchronize(f->stream));
+  return MM_OK;
+}
+
+int mm_fno_set_params(mm_fno* f, const float* host, long long n) {
+  if (!f || !host || n != f->nparam) return ffail(MM_ERR_ARG, "bad arguments");
+  MMF_CUDA(cudaMemcpyAsync(f->prm, host, n * sizeof(float), cudaMemcpyHostToDevice, f->stream));
+  MMF_CUDA(cudaMemsetAsync(f->m1, 0, n * sizeof(float), f->stream));
+  MMF_CUDA(cudaMemsetAsync(f->m2, 0, n * sizeof(float), f->stream));
+  MMF_CUDA(cudaStreamSynchronize(f->stream));
+  f->adam_t = 0;
+  return MM_OK;
+}
+
+int mm_fno_forward(mm_fno* f, const float* u, float* y, int S) {
+  if (!f || !u || !y || S < 1 || S > f->Smax) return ffail(MM_ERR_ARG, "bad arguments");
+  MMF_CUDA(cudaMemcpyAsync(f->u, u, (size_t)S * 3 * f->N * sizeof(float), cudaMemcpyDeviceToDevice, f->stream));
+  fwd(f, S);
+  MMF_CUDA(cudaMemcpyAsync(y, f->yh, (size_t)S * 3 * f->N * sizeof(float), cudaMemcpyDeviceToDevice, f->stream));
+  MMF_CUDA(cudaGetLastError());
+  MMF_CUDA(cudaStreamSynchronize(f->stream));
+  return MM_OK;
+}
+
+int mm_fno_grad(mm_fno* f, const float* u, const float* y, int S, float* grad_host, double* loss) {
+  if (!f || !u || !y || S < 1 || S > f->Smax) return ffail(MM_ERR_ARG, "bad arguments");
+  MMF_CUDA(cudaMemcpyAsync(f->u, u, (size_t)S * 3 * f->N * sizeof(float), cudaMemcpyDeviceToDevice, f->stream));
+  fwd(f, S);
+  bwd(f, S, y);
+  MMF_CUDA(cudaGetLastError());
+  double acc[2];
+  MMF_CUDA(cudaMemcpyAsync(acc, f->acc, sizeof(acc), cudaMemcpyDeviceToHost, f->stream));
+  if (grad_host) MMF_CUDA(cudaMemcpyAsync(grad_host, f->grd, f->nparam * sizeof(float), cudaMemcpyDeviceToHost, f->stream));
+  MMF_CUDA(cudaStreamSynchronize(f->stream));
+  if (loss) *loss = acc[0] / acc[1];
+  return MM_OK;
+}
+
+int mm_fno_train_step(mm_fno* f, const float* u, const float* y, int S, double lr, double* loss) {
+  int rc = mm_fno_grad(f, u, y, S, nullptr, loss);
+  if (rc) return rc;
+  f->adam_t++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)f->adam_t), c2 = 1.f - std::pow(b2, (float)f->adam_t);
+  k_adam<<<nb(f->nparam), 256, 0, f->stream>>>(f->nparam, f->prm, f->grd, f->m1, f->m2, (float)lr, b1, b2, 1e-8f, c1, c2);
+  MMF_CUDA(cudaGetLastError());
+  MMF_CUDA(cudaStreamSynchronize(f->stream));
+  return MM_OK;
+}
+
+}  // extern "C"
+
+namespace mm {
+// surrogate demag field for a context: u from m, FNO forward, B = mu0 ms_ref y
+void launch_fno_demag(mm_fno* f, const Geom& g, const Buffers& b, const float* m, float inv_ref, float mu0_ref,
+                      float* bd, cudaStream_t s) {
+  cudaStream_t keep = f->stream;
+  f->stream = s;
+  k_to_u<<<nb(g.n), 256, 0, s>>>(g.n, m, b.mask, b.region, b.lut, inv_ref, f->u);
+  fwd(f, 1);
+  k_scale<<<nb(3 * g.n), 256, 0, s>>>(3 * g.n, f->yh, mu0_ref, bd);
+  f->stream = keep;
+}
+void launch_rel_err(long long n, const float* a, const float* b, double* acc, cudaStream_t s) {
+  cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+  k_rel_err<<<512, 256, 0, s>>>(n, a, b, acc);
+}
+bool fno_matches(mm_fno* f, const Geom& g) { return f && f->H == g.ny && f->W == g.nx && g.nz == 1; }
+void launch_to_u(const Geom& g, const Buffers& b, const float* m, float inv_ref, float* u, cudaStream_t s) {
+  k_to_u<<<nb(g.n), 256, 0, s>>>(g.n, m, b.mask, b.region, b.lut, inv_ref, u);
+}
+void launch_scale(long long n, const float* x, float a, float* y, cudaStream_t s) {
+  k_scale<<<nb(n), 256, 0, s>>>(n, x, a, y);
+}
+}  // namespace mm

@@ -78,6 +78,15 @@ struct mm_ctx {
   int fixed_n = 0;   // host copy of the replay length
   long long launches = 0;        // kernels launched (host count)
   long long graph_nodes = 0;     // kernels per captured attempt
+  // learned demag surrogate (fno.cu) with the exact path as guard
+  mm_fno* sur = nullptr;
+  bool sur_active = false;
+  int sur_every = 10;
+  double sur_tol = 1e-3;
+  float sur_inv_ref = 0.f, sur_mu0_ref = 0.f;
+  long long sur_steps = 0, sur_checks = 0, sur_fallbacks = 0;
+  double sur_last_err = 0.0;
+  double* sur_acc = nullptr;   // device, 2 doubles
 };
 
 namespace {
@@ -141,18 +150,27 @@ int demag_launches(const Geom& g) {
   return 2 + mid;
 }
 
+// demag field of the stage input: exact convolution, or the surrogate
+void enqueue_demag(mm_ctx* c) {
+  if (!c->T.demag) return;
+  if (c->sur_active)
+    launch_fno_demag(c->sur, c->g, c->b, c->b.ms, c->sur_inv_ref, c->sur_mu0_ref, c->b.bd, c->stream);
+  else
+    launch_demag(c->g, c->b, c->b.ms, c->stream);
+}
+
 // stage-1 torque at the current m (FSAL start)
 void enqueue_k1(mm_ctx* c) {
   c->launches += 2 + (c->T.demag ? demag_launches(c->g) : 0);
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
-  if (c->T.demag) launch_demag(c->g, c->b, c->b.ms, c->stream);
+  enqueue_demag(c);
   launch_torque_t(c->g, c->b, c->T, 0, c->freq, c->phase, c->stream);
 }
 
 void enqueue_attempt(mm_ctx* c) {
   for (int s = 1; s < 7; ++s) {
     launch_stage_input(c->g, c->b, s, c->stream);
-    if (c->T.demag) launch_demag(c->g, c->b, c->b.ms, c->stream);
+    enqueue_demag(c);
     launch_torque_t(c->g, c->b, c->T, s, c->freq, c->phase, c->stream);
   }
   launch_error_control(c->g, c->b, c->stream);
@@ -386,7 +404,8 @@ int mm_destroy(mm_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   Buffers& b = c->b;
   void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.bd, b.out,
-                  b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed};
+                  b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed,
+                  c->sur_acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -554,18 +573,58 @@ int mm_set_fixed_dt_sequence(mm_ctx* c, const double* dts, int n) {
   return write_state(c);
 }
 
+// Exact-path judge of the surrogate: relative L2 difference of the two
+// demag fields at the current m; above the tolerance the context falls back
+// to the exact convolution for the rest of its life.
+static int surrogate_check(mm_ctx* c) {
+  Buffers nb = c->b;
+  nb.st = nullptr;
+  launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
+  launch_demag(c->g, nb, c->b.ms, c->stream);                     // exact -> bd
+  launch_fno_demag(c->sur, c->g, c->b, c->b.ms, c->sur_inv_ref, c->sur_mu0_ref, c->b.out, c->stream);
+  launch_rel_err(3 * c->g.n, c->b.out, c->b.bd, c->sur_acc, c->stream);
+  double acc[2];
+  MM_CUDA(cudaMemcpyAsync(acc, c->sur_acc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->sur_checks++;
+  c->sur_last_err = acc[1] > 0 ? std::sqrt(acc[0] / acc[1]) : 0.0;
+  if (!(c->sur_last_err <= c->sur_tol)) {
+    c->sur_active = false;
+    c->sur_fallbacks++;
+    c->graph_valid = false;
+    c->k1_valid = false;   // the cached first stage used the surrogate field
+  }
+  return MM_OK;
+}
+
 int mm_step(mm_ctx* c, int n) {
   if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
   if (n < 0) return fail(MM_ERR_ARG, "n must be >= 0");
   if (n == 0) return MM_OK;
   const int mode = c->fixed_n > 0 ? 2 : 0;
-  return drive(c, mode, n, 0.0);
+  if (!c->sur_active) return drive(c, mode, n, 0.0);
+  // surrogate mode: chunks of sur_every steps, each judged by the exact path
+  int left = n;
+  while (left > 0) {
+    const int chunk = c->sur_active ? std::min(left, c->sur_every) : left;
+    const bool was_active = c->sur_active;
+    int rc = drive(c, mode, chunk, 0.0);
+    if (rc) return rc;
+    if (was_active) c->sur_steps += chunk;
+    left -= chunk;
+    if (c->sur_active) {
+      rc = surrogate_check(c);
+      if (rc) return rc;
+    }
+  }
+  return MM_OK;
 }
 
 int mm_run(mm_ctx* c, double t_end) {
   if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
   if (!std::isfinite(t_end)) return fail(MM_ERR_ARG, "t_end must be finite");
   if (c->fixed_n > 0) return fail(MM_ERR_STATE, "run() is not available in replay mode");
+  if (c->sur_active) return fail(MM_ERR_STATE, "run() is not available with the demag surrogate; use mm_step");
   return drive(c, 1, 0, t_end);
 }
 
@@ -746,6 +805,164 @@ int mm_demag_apply(mm_ctx* c, const float* m, float* b) {
   launch_demag(c->g, nb, m, c->stream);
   MM_CUDA(cudaGetLastError());
   MM_CUDA(cudaStreamSynchronize(c->stream));
+  return MM_OK;
+}
+
+int mm_set_demag_surrogate(mm_ctx* c, mm_fno* net, double ms_ref, int check_every, double fallback_rel_err) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (!net) {
+    c->sur = nullptr;
+    c->sur_active = false;
+    c->graph_valid = false;
+    c->k1_valid = false;
+    return MM_OK;
+  }
+  if (!fno_matches(net, c->g)) return fail(MM_ERR_ARG, "surrogate grid differs from the context (2-D, same nx, ny)");
+  if (!(ms_ref > 0) || check_every < 1 || !(fallback_rel_err > 0)) return fail(MM_ERR_ARG, "bad surrogate settings");
+  if (!c->sur_acc) MM_CUDA(cudaMalloc((void**)&c->sur_acc, 2 * sizeof(double)));
+  c->sur = net;
+  c->sur_active = true;
+  c->sur_every = check_every;
+  c->sur_tol = fallback_rel_err;
+  c->sur_inv_ref = (float)(1.0 / ms_ref);
+  c->sur_mu0_ref = (float)(4e-7 * kPi * ms_ref);
+  c->sur_steps = c->sur_checks = c->sur_fallbacks = 0;
+  c->graph_valid = false;
+  c->k1_valid = false;
+  return MM_OK;
+}
+
+// Training pairs from the context's own exact trajectories, then Adam epochs
+// on the GPU.  Each trajectory starts from m uniform on the sphere per cell
+// under a static field of uniform direction and magnitude U[0, field_max];
+// consecutive pairs are steps_between exact RK45 steps apart.  The context's
+// m, time, fields and surrogate setting are restored afterwards.
+int mm_surrogate_train(mm_ctx* c, mm_fno* net, double ms_ref, int n_pairs, int traj_len, int steps_between,
+                       double field_max, int epochs, int batch, double lr, unsigned long long seed,
+                       double* final_loss) {
+  if (!c || !net) return fail(MM_ERR_ARG, "NULL argument");
+  if (!fno_matches(net, c->g)) return fail(MM_ERR_ARG, "surrogate grid differs from the context (2-D, same nx, ny)");
+  if (!(ms_ref > 0) || n_pairs < 1 || traj_len < 1 || steps_between < 0 || epochs < 0 || batch < 1 || !(lr > 0))
+    return fail(MM_ERR_ARG, "bad training settings");
+  const long long n3 = 3 * c->g.n;
+  // save state
+  std::vector<float> m_save(n3);
+  int rc = mm_get_m(c, m_save.data());
+  if (rc) return rc;
+  double t_save, dt_save;
+  rc = mm_get_time(c, &t_save, &dt_save);
+  if (rc) return rc;
+  double b0_save[kRegions][3], b1_save[kRegions][3];
+  std::memcpy(b0_save, c->b0, sizeof(b0_save));
+  std::memcpy(b1_save, c->b1, sizeof(b1_save));
+  mm_fno* sur_save = c->sur;
+  const bool active_save = c->sur_active;
+  c->sur_active = false;
+  c->graph_valid = false;
+  c->k1_valid = false;
+  float *U = nullptr, *Y = nullptr;
+  cudaError_t e = cudaMalloc((void**)&U, (size_t)n_pairs * n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Y, (size_t)n_pairs * n3 * sizeof(float));
+  auto done = [&](int code) {
+    cudaFree(U);
+    cudaFree(Y);
+    std::memcpy(c->b0, b0_save, sizeof(b0_save));
+    std::memcpy(c->b1, b1_save, sizeof(b1_save));
+    c->lut_dirty = true;
+    mm_set_m(c, m_save.data());
+    mm_set_time(c, t_save, dt_save);
+    c->sur = sur_save;
+    c->sur_active = active_save && sur_save;
+    c->graph_valid = false;
+    c->k1_valid = false;
+    return code;
+  };
+  if (e != cudaSuccess) return done(fail(MM_ERR_OOM, "no room for the training pairs"));
+  unsigned long long st = seed * 0x9E3779B97F4A7C15ULL + 7;
+  auto unif = [&]() {   // splitmix64 -> (0, 1)
+    st += 0x9E3779B97F4A7C15ULL;
+    unsigned long long z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  auto normal = [&]() { return std::sqrt(-2.0 * std::log(unif())) * std::cos(2.0 * kPi * unif()); };
+  std::vector<float> m0(n3);
+  Buffers nb = c->b;
+  nb.st = nullptr;
+  const float inv_ref = (float)(1.0 / ms_ref), inv_mu = (float)(1.0 / (4e-7 * kPi * ms_ref));
+  for (int p = 0; p < n_pairs; ++p) {
+    if (p % traj_len == 0) {
+      const long long n = c->g.n;
+      for (long long i = 0; i < n; ++i) {
+        double v[3] = {normal(), normal(), normal()};
+        const double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int k = 0; k < 3; ++k) m0[k * n + i] = (float)(v[k] / r);
+      }
+      double d[3] = {normal(), normal(), normal()};
+      const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const double mag = field_max * unif();
+      for (int reg = 0; reg < kRegions; ++reg)
+        for (int k = 0; k < 3; ++k) {
+          c->b0[reg][k] = mag * d[k] / r;
+          c->b1[reg][k] = 0.0;
+        }
+      c->lut_dirty = true;
+      rc = mm_set_m(c, m0.data());
+      if (rc == MM_OK) rc = mm_set_time(c, 0.0, 1e-14);
+      if (rc) return done(rc);
+    } else if (steps_between > 0) {
+      rc = mm_step(c, steps_between);
+      if (rc) return done(rc);
+    }
+    // pair: u = Msat m / ms_ref, y = B_demag / (mu0 ms_ref), exact convolution
+    launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
+    launch_to_u(c->g, c->b, c->b.ms, inv_ref, U + (size_t)p * n3, c->stream);
+    launch_demag(c->g, nb, c->b.ms, c->stream);
+    launch_scale(n3, c->b.bd, inv_mu, Y + (size_t)p * n3, c->stream);
+  }
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  // training: shuffled mini-batches, pairs gathered into contiguous staging
+  float *ub = nullptr, *yb = nullptr;
+  e = cudaMalloc((void**)&ub, (size_t)batch * n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&yb, (size_t)batch * n3 * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaFree(ub);
+    cudaFree(yb);
+    return done(fail(MM_ERR_OOM, "no room for the training batch"));
+  }
+  std::vector<int> order(n_pairs);
+  for (int i = 0; i < n_pairs; ++i) order[i] = i;
+  double last = 0.0;
+  for (int ep = 0; ep < epochs && rc == MM_OK; ++ep) {
+    for (int i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[(int)(unif() * (i + 1)) % (i + 1)]);
+    for (int b0i = 0; b0i < n_pairs && rc == MM_OK; b0i += batch) {
+      const int S = std::min(batch, n_pairs - b0i);
+      for (int j = 0; j < S; ++j) {
+        cudaMemcpyAsync(ub + (size_t)j * n3, U + (size_t)order[b0i + j] * n3, n3 * sizeof(float),
+                        cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(yb + (size_t)j * n3, Y + (size_t)order[b0i + j] * n3, n3 * sizeof(float),
+                        cudaMemcpyDeviceToDevice, c->stream);
+      }
+      cudaStreamSynchronize(c->stream);
+      rc = mm_fno_train_step(net, ub, yb, S, lr, &last);
+    }
+  }
+  cudaFree(ub);
+  cudaFree(yb);
+  if (final_loss) *final_loss = last;
+  return done(rc);
+}
+
+int mm_get_surrogate_stats(mm_ctx* c, long long* steps, long long* checks, long long* fallbacks, double* last_err,
+                           int* active) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (steps) *steps = c->sur_steps;
+  if (checks) *checks = c->sur_checks;
+  if (fallbacks) *fallbacks = c->sur_fallbacks;
+  if (last_err) *last_err = c->sur_last_err;
+  if (active) *active = c->sur_active ? 1 : 0;
   return MM_OK;
 }
 

@@ -140,4 +140,14 @@ void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const f
                         double phase, cudaStream_t s);
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s);
 
+// FNO surrogate (fno.cu)
+}  // namespace mm
+struct mm_fno;
+namespace mm {
+void launch_fno_demag(mm_fno* f, const Geom& g, const Buffers& b, const float* m, float inv_ref, float mu0_ref,
+                      float* bd, cudaStream_t s);
+void launch_rel_err(long long n, const float* a, const float* b, double* acc, cudaStream_t s);
+bool fno_matches(mm_fno* f, const Geom& g);
+void launch_to_u(const Geom& g, const Buffers& b, const float* m, float inv_ref, float* u, cudaStream_t s);
+void launch_scale(long long n, const float* x, float a, float* y, cudaStream_t s);
 }  // namespace mm

@@ -51,6 +51,11 @@ class mm_instance_spec(C.Structure):
                 ("gamma_ll", C.c_double), ("bext", C.c_double * 3)]
 
 
+class mm_fno_cfg(C.Structure):
+    _fields_ = [("width", C.c_int), ("layers", C.c_int), ("modes_x", C.c_int), ("modes_y", C.c_int),
+                ("max_batch", C.c_int), ("seed", C.c_ulonglong)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -97,6 +102,18 @@ _SIGS = {
     "mm_batch_get_stats": (_I, [_P, _I, C.POINTER(mm_stats)]),
     "mm_batch_get_dt_history": (_I, [_P, _I, _P, _I, C.POINTER(_I)]),
     "mm_batch_num_classes": (_I, [_P]),
+    "mm_fno_create": (_I, [C.POINTER(_P), _I, _I, C.POINTER(mm_fno_cfg), _I, _P]),
+    "mm_fno_destroy": (_I, [_P]),
+    "mm_fno_param_count": (C.c_longlong, [_P]),
+    "mm_fno_get_params": (_I, [_P, _P, C.c_longlong]),
+    "mm_fno_set_params": (_I, [_P, _P, C.c_longlong]),
+    "mm_fno_forward": (_I, [_P, _P, _P, _I]),
+    "mm_fno_grad": (_I, [_P, _P, _P, _I, _P, C.POINTER(_D)]),
+    "mm_fno_train_step": (_I, [_P, _P, _P, _I, _D, C.POINTER(_D)]),
+    "mm_surrogate_train": (_I, [_P, _P, _D, _I, _I, _I, _D, _I, _I, _D, C.c_ulonglong, C.POINTER(_D)]),
+    "mm_set_demag_surrogate": (_I, [_P, _P, _D, _I, _D]),
+    "mm_get_surrogate_stats": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                    C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_I)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -274,6 +291,23 @@ class Context:
     def sync(self):
         _check(mm_sync(self.h))
 
+    def set_demag_surrogate(self, net, ms_ref, check_every=10, fallback_rel_err=1e-3):
+        _check(mm_set_demag_surrogate(self.h, None if net is None else net.h, ms_ref, check_every,
+                                      fallback_rel_err))
+
+    def surrogate_stats(self):
+        a, b, c_ = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        e, act = C.c_double(), C.c_int()
+        _check(mm_get_surrogate_stats(self.h, C.byref(a), C.byref(b), C.byref(c_), C.byref(e), C.byref(act)))
+        return {"steps": a.value, "checks": b.value, "fallbacks": c_.value, "last_rel_err": e.value,
+                "active": bool(act.value)}
+
+    def train_surrogate(self, net, ms_ref, n_pairs, traj_len, steps_between, field_max, epochs, batch, lr, seed=0):
+        loss = C.c_double()
+        _check(mm_surrogate_train(self.h, net.h, ms_ref, n_pairs, traj_len, steps_between, field_max, epochs, batch,
+                                  lr, seed, C.byref(loss)))
+        return loss.value
+
     # --- configuration from a Problem description ---
     @classmethod
     def from_problem(cls, p, device=0, stream=None, regions_used=None):
@@ -358,3 +392,55 @@ class Batch:
 
     def num_classes(self):
         return mm_batch_num_classes(self.h)
+
+
+class FNO:
+    """Fourier-neural-operator demag surrogate on the GPU (mm_fno_*)."""
+
+    def __init__(self, ny, nx, width=32, layers=4, modes_x=24, modes_y=24, max_batch=4, seed=0, device=0,
+                 stream=None):
+        cfg = mm_fno_cfg(width, layers, modes_x, modes_y, max_batch, seed)
+        h = C.c_void_p()
+        _check(mm_fno_create(C.byref(h), ny, nx, C.byref(cfg), device, stream))
+        self.h = h
+        self.shape = (ny, nx)
+        self.cfg = dict(width=width, layers=layers, modes_x=modes_x, modes_y=modes_y)
+
+    def close(self):
+        if self.h:
+            mm_fno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nparams(self):
+        return mm_fno_param_count(self.h)
+
+    def get_params(self):
+        out = np.zeros(self.nparams(), dtype=np.float32)
+        _check(mm_fno_get_params(self.h, _ptr(out), out.size))
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        _check(mm_fno_set_params(self.h, _ptr(a), a.size))
+
+    def forward(self, u_dev, y_dev, S):
+        _check(mm_fno_forward(self.h, C.c_void_p(u_dev.data_ptr()), C.c_void_p(y_dev.data_ptr()), S))
+
+    def grad(self, u_dev, y_dev, S):
+        g = np.zeros(self.nparams(), dtype=np.float32)
+        loss = C.c_double()
+        _check(mm_fno_grad(self.h, C.c_void_p(u_dev.data_ptr()), C.c_void_p(y_dev.data_ptr()), S, _ptr(g),
+                           C.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, u_dev, y_dev, S, lr):
+        loss = C.c_double()
+        _check(mm_fno_train_step(self.h, C.c_void_p(u_dev.data_ptr()), C.c_void_p(y_dev.data_ptr()), S, lr,
+                                 C.byref(loss)))
+        return loss.value

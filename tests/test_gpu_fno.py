@@ -1,0 +1,127 @@
+"""FNO demag surrogate on the GPU: forward and gradients against the float64
+oracle (same parameters), training on the context's own exact trajectories,
+and the exact-path guard inside the RK45 loop.
+
+Tolerances: the dense products round their operands to bfloat16 (8-bit
+mantissa, relative rounding 2^-9 = 2e-3 per operand), so outputs and
+gradients are compared in relative L2 norm at 2e-2 with cosine >= 0.999."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.fno import backward, dft_mats, forward, init_params, loss  # noqa: E402
+from paper_1406_7635_gb300.workloads import Problem, film_sp4  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def mm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1406_7635_gb300.build import build
+    build()
+    from paper_1406_7635_gb300 import mm as _mm
+    return _mm
+
+
+def flatten(params, L):
+    """Oracle parameters in the library's flat order (P, p, {W, b, R}, Q, q)."""
+    parts = [params["P"].ravel(), params["p"]]
+    for l in range(L):
+        R = params[f"R{l}"]
+        parts += [params[f"W{l}"].ravel(), params[f"b{l}"], np.stack([R.real, R.imag], axis=-1).ravel()]
+    parts += [params["Q"].ravel(), params["q"]]
+    return np.concatenate(parts)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def cosine(a, b):
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_forward_and_gradients_vs_oracle(mm, S):
+    C, L, H, W, Mx, My = 4, 2, 8, 8, 3, 3
+    rng = np.random.default_rng(21)
+    params = init_params(C, L, Mx, My, seed=4)
+    for k in list(params):
+        if k.startswith("b") or k in ("p", "q"):
+            params[k] = 0.1 * rng.standard_normal(params[k].shape)
+    mats = dft_mats(H, W, Mx, My)
+    u = rng.standard_normal((S, 3, H, W))
+    y = rng.standard_normal((S, 3, H, W))
+    # oracle: batch loss = sum over samples / sum |y|^2
+    yh = [forward(params, u[s], L, mats) for s in range(S)]
+    ysq = float(np.sum(y * y))
+    oracle_loss = sum(float(np.sum((yh[s][0] - y[s]) ** 2)) for s in range(S)) / ysq
+    grads = None
+    for s in range(S):
+        g = backward(params, yh[s][1], yh[s][0], y[s], L, mats)
+        # backward() normalises by this sample's |y|^2; rescale to the batch sum
+        scale = float(np.sum(y[s] * y[s])) / ysq
+        g = {k: v * scale for k, v in g.items()}
+        grads = g if grads is None else {k: grads[k] + g[k] for k in g}
+    g_ora = flatten(grads, L)
+
+    net = mm.FNO(H, W, width=C, layers=L, modes_x=Mx, modes_y=My, max_batch=S)
+    net.set_params(flatten(params, L).astype(np.float32))
+    ud = torch.tensor(u.astype(np.float32), device="cuda").contiguous()
+    yd = torch.tensor(y.astype(np.float32), device="cuda").contiguous()
+    out = torch.empty_like(ud)
+    net.forward(ud, out, S)
+    y_gpu = out.cpu().numpy().astype(np.float64)
+    assert rel(y_gpu, np.stack([yh[s][0] for s in range(S)])) < 2e-2
+    g_gpu, l_gpu = net.grad(ud, yd, S)
+    assert abs(l_gpu - oracle_loss) < 2e-2 * oracle_loss
+    # per parameter group
+    off = 0
+    for name, size in [("P", C * 3), ("p", C)] + sum(
+            [[(f"W{l}", C * C), (f"b{l}", C), (f"R{l}", 2 * C * C * 2 * My * Mx)] for l in range(L)], []) + [
+            ("Q", 3 * C), ("q", 3)]:
+        a, b = g_gpu[off:off + size].astype(np.float64), g_ora[off:off + size]
+        off += size
+        assert cosine(a, b) >= 0.999, name
+        assert rel(a, b) <= 2e-2, name
+    net.close()
+
+
+def test_training_on_exact_trajectories_reduces_loss(mm):
+    p = film_sp4(64, 64)
+    ctx = mm.Context.from_problem(p)
+    net = mm.FNO(64, 64, width=16, layers=2, modes_x=12, modes_y=12, max_batch=4, seed=3)
+    first = ctx.train_surrogate(net, 8e5, n_pairs=16, traj_len=8, steps_between=5, field_max=50e-3,
+                                epochs=1, batch=4, lr=1e-3, seed=1)
+    last = ctx.train_surrogate(net, 8e5, n_pairs=16, traj_len=8, steps_between=5, field_max=50e-3,
+                               epochs=20, batch=4, lr=1e-3, seed=1)
+    assert last < 0.8 * first, (first, last)
+    # the context's own state is restored
+    assert np.abs(ctx.get_m() - p.m0.astype(np.float32)).max() < 1e-6
+    net.close()
+    ctx.close()
+
+
+def test_guard_falls_back_to_exact_path(mm):
+    p = film_sp4(64, 32)
+    net = mm.FNO(32, 64, width=8, layers=2, modes_x=8, modes_y=8, max_batch=1, seed=5)
+    # untrained network, tight bound: the first check fails, the rest is exact
+    ctx = mm.Context.from_problem(p)
+    ctx.set_demag_surrogate(net, 8e5, check_every=5, fallback_rel_err=1e-3)
+    ctx.step(20)
+    st = ctx.surrogate_stats()
+    assert st["checks"] == 1 and st["fallbacks"] == 1 and not st["active"] and st["steps"] == 5
+    assert st["last_rel_err"] > 1e-3
+    # loose bound: the surrogate stays in charge and is judged every 5 steps
+    ctx2 = mm.Context.from_problem(p)
+    ctx2.set_demag_surrogate(net, 8e5, check_every=5, fallback_rel_err=1e9)
+    ctx2.step(20)
+    st2 = ctx2.surrogate_stats()
+    assert st2["checks"] == 4 and st2["fallbacks"] == 0 and st2["active"] and st2["steps"] == 20
+    with pytest.raises(mm.MMError):
+        ctx2.run(1e-9)
+    ctx.close()
+    ctx2.close()
+    net.close()
