@@ -65,6 +65,18 @@ struct BPtrs {
   float* k[7];
 };
 
+__device__ __forceinline__ float* bpick(const BPtrs& p, int j) {
+  switch (j) {
+    case 0: return p.k[0];
+    case 1: return p.k[1];
+    case 2: return p.k[2];
+    case 3: return p.k[3];
+    case 4: return p.k[4];
+    case 5: return p.k[5];
+    default: return p.k[6];
+  }
+}
+
 __device__ __forceinline__ int role(int j, int parity) {
   return j == 0 ? (parity ? 6 : 0) : (j == 6 ? (parity ? 0 : 6) : j);
 }
@@ -103,7 +115,7 @@ __global__ void k_b_stage_input(Geom g, BPtrs p, float* __restrict__ ms, const I
   for (int j = 0; j < s; ++j) {
     const float a = S.ah[s][j];
     if (a == 0.0f) continue;
-    const float* __restrict__ k = p.k[role(j, par)] + o;
+    const float* __restrict__ k = bpick(p, role(j, par)) + o;
     a0 = fmaf(a, k[i], a0);
     a1 = fmaf(a, k[g.n + i], a1);
     a2 = fmaf(a, k[2 * g.n + i], a2);
@@ -142,7 +154,7 @@ __global__ void k_b_torque(Geom g, BPtrs p, const float* __restrict__ ms, const 
   if (z < g.nz - 1) nb(i + sz, g.idz2);
   const float cx = my * bz - mz * by, cy = mz * bx - mx * bz, cz = mx * by - my * bx;
   const float dx = my * cz - mz * cy, dy = mz * cx - mx * cz, dz = mx * cy - my * cx;
-  float* __restrict__ k = p.k[role(s, S.parity)] + o;
+  float* __restrict__ k = bpick(p, role(s, S.parity)) + o;
   k[i] = P.gfac * (cx + P.alpha * dx);
   k[g.n + i] = P.gfac * (cy + P.alpha * dy);
   k[2 * g.n + i] = P.gfac * (cz + P.alpha * dz);
@@ -197,7 +209,7 @@ __global__ void k_b_error(Geom g, BPtrs p, const float* __restrict__ ms, InstSta
     for (int j = 0; j < 7; ++j) {
       const float c = S.eh[j];
       if (c == 0.0f) continue;
-      const float* __restrict__ k = p.k[role(j, par)] + o;
+      const float* __restrict__ k = bpick(p, role(j, par)) + o;
       ex = fmaf(c, k[i], ex);
       ey = fmaf(c, k[g.n + i], ey);
       ez = fmaf(c, k[2 * g.n + i], ez);

@@ -137,8 +137,11 @@ __host__ __device__ constexpr int ns_of(int L, int p) {
 // consecutive pencils (with an odd row pitch this avoids bank conflicts).
 // tw holds W_TWL^i = exp(-2 pi i i / TWL) for i < TWL (TWL a multiple of L):
 // the global 2048-entry table, or a per-length copy in shared memory.
+// pre (first pass only, may be null): input element i is multiplied by pre[i]
+// as it is loaded.
 template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL>
-__device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw,
+                                              const float2* __restrict__ pre = nullptr) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
   constexpr int PER = (TOT + NT - 1) / NT;
@@ -151,6 +154,10 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
       const int base = (p / INNER) * BS + (p % INNER);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q][r] = s[base + (j + r * NB) * ES];
+      if (NS == 1 && pre != nullptr) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = cmul(v[q][r], pre[j + r * NB]);
+      }
     }
   }
   __syncthreads();
@@ -187,14 +194,15 @@ template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL = k
 struct FftG;
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, false> {
-  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw) {
-    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL>(s, tw);
+  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw,
+                                             const float2* __restrict__ pre = nullptr) {
+    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL>(s, tw, P == 0 ? pre : nullptr);
     FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P + 1>::run(s, tw);
   }
 };
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, true> {
-  __device__ __forceinline__ static void run(float2*, const float2* __restrict__) {}
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr) {}
 };
 
 // pencils stored as rows with pitch PST, twiddles from the global table

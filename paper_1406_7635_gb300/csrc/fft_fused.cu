@@ -156,30 +156,6 @@ __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ 
 }
 
 // ----------------------------------------------------------------------------
-// kernel multiply (octant lookup with mirror signs; x never mirrors)
-// ----------------------------------------------------------------------------
-// ktf holds the octant per kx plane, ky fastest: ktf[kx][c][iz][iy]
-__device__ __forceinline__ void kmul(const Geom& g, const float* __restrict__ ktf, int kx, int ky, int kz, float2& X,
-                                     float2& Y, float2& Z) {
-  int iy = ky, iz = kz;
-  float sy = 1.f, sz = 1.f;
-  if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
-  if (kz > g.pz / 2) { iz = g.pz - kz; sz = -1.f; }
-  const long long per = (long long)g.hky * g.hkz;
-  const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
-  const float kxx = __ldg(&ktf[o]), kyy = __ldg(&ktf[per + o]), kzz = __ldg(&ktf[2 * per + o]);
-  const float kxy = sy * __ldg(&ktf[3 * per + o]);
-  const float kxz = sz * __ldg(&ktf[4 * per + o]);
-  const float kyz = sy * sz * __ldg(&ktf[5 * per + o]);
-  const float2 bx = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
-  const float2 by = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
-  const float2 bz = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
-  X = bx;
-  Y = by;
-  Z = bz;
-}
-
-// ----------------------------------------------------------------------------
 // k_yz: plane [3][LZ][LY] in shared memory, y fastest, rows padded to an
 // odd pitch RP = LY + 1 (conflict-free row and column transforms)
 // ----------------------------------------------------------------------------
@@ -213,34 +189,67 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
   const int ry = rank % g.cly, rz = rank / g.cly;
   const int kx = (blockIdx.x / CL) % g.hx;
-  // 1. load and twiddle by exp(-2 pi i (y ry / py + z rz / pz))
-#pragma unroll 4
+  // 1. load the plane (asynchronous copies, all in flight at once); rows and
+  //    columns past the grid are zero
   for (int e = threadIdx.x; e < 3 * PL; e += NT) {
     const int y = e % LY, z = (e / LY) % LZ, c = e / PL;
-    float2 v = make_float2(0.f, 0.f);
+    float2* dst = s + c * CS + z * RP + y;
     if (y < g.ny && z < g.nz) {
-      v = spec[tidx(g, c, kx, z, y)];
-      if (ry) v = cmul(v, rty[y]);
-      if (rz) v = cmul(v, rtz[z]);
+      const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(spec + tidx(g, c, kx, z, y)));
+    } else {
+      *dst = make_float2(0.f, 0.f);
     }
-    s[c * CS + z * RP + y] = v;
   }
+  asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
   // 2. forward transforms along y (LZ rows) and z (LY columns), one
-  //    component at a time (fewer values held in registers per pass)
+  //    component at a time; the class twiddle exp(-2 pi i (y ry / py +
+  //    z rz / pz)) is applied as the first pass loads its inputs
   for (int c = 0; c < 3; ++c) {
-    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
-    FftG<LZ, -1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz);
+    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
+    FftG<LZ, -1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz, rz ? rtz : nullptr);
   }
-  // 3. multiply by the kernel at (kx, ky = CLY j + ry, kz = CLZ l + rz)
-  for (int e = threadIdx.x; e < PL; e += NT) {
-    const int j = e % LY, l = e / LY;
-    const int a = l * RP + j;
-    float2 X = s[a], Y = s[CS + a], Z = s[2 * CS + a];
-    kmul(g, kt, kx, g.cly * j + ry, g.clz * l + rz, X, Y, Z);
-    s[a] = X;
-    s[CS + a] = Y;
-    s[2 * CS + a] = Z;
+  // 3. multiply by the kernel at (kx, ky = CLY j + ry, kz = CLZ l + rz);
+  //    (ktf holds the octant per kx plane, ky fastest: ktf[kx][c][iz][iy];
+  //    mirror signs: Nxy odd in y, Nxz odd in z, Nyz odd in both); the
+  //    coefficient loads of CH points are issued together
+  constexpr int PPT = (PL + NT - 1) / NT;   // points per thread
+  constexpr int CH = PPT < 2 ? PPT : 2;
+#pragma unroll
+  for (int q0 = 0; q0 < PPT; q0 += CH) {
+    float kc[CH][6];
+    float sgn[CH][2];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int e = threadIdx.x + (q0 + q) * NT;
+      if (e >= PL) continue;
+      const int j = e % LY, l = e / LY;
+      const int ky = g.cly * j + ry, kz = g.clz * l + rz;
+      int iy = ky, iz = kz;
+      float sy = 1.f, sz = 1.f;
+      if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
+      if (kz > g.pz / 2) { iz = g.pz - kz; sz = -1.f; }
+      const long long per = (long long)g.hky * g.hkz;
+      const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) kc[q][t] = __ldg(&kt[t * per + o]);
+      sgn[q][0] = sy;
+      sgn[q][1] = sz;
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int e = threadIdx.x + (q0 + q) * NT;
+      if (e >= PL) continue;
+      const int j = e % LY, l = e / LY;
+      const int a = l * RP + j;
+      const float kxx = kc[q][0], kyy = kc[q][1], kzz = kc[q][2];
+      const float kxy = sgn[q][0] * kc[q][3], kxz = sgn[q][1] * kc[q][4], kyz = sgn[q][0] * sgn[q][1] * kc[q][5];
+      const float2 X = s[a], Y = s[CS + a], Z = s[2 * CS + a];
+      s[a] = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+      s[CS + a] = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+      s[2 * CS + a] = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+    }
   }
   __syncthreads();
   // 4. inverse transforms
@@ -248,21 +257,9 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
     FftG<LZ, 1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz);
     FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
   }
-  // 5. undo the twiddle on the outputs that are kept (y < ny, z < nz)
-  if (ry || rz) {
-    for (int e = threadIdx.x; e < 3 * PL; e += NT) {
-      const int y = e % LY, z = (e / LY) % LZ, c = e / PL;
-      if (y < g.ny && z < g.nz) {
-        const int a = c * CS + z * RP + y;
-        float2 v = s[a];
-        if (ry) v = cmul(v, cconj(rty[y]));
-        if (rz) v = cmul(v, cconj(rtz[z]));
-        s[a] = v;
-      }
-    }
-  }
-  // 6. sum the class contributions across the cluster; each block stores one
-  //    contiguous 1/CL share of the plane
+  // 5. sum the class contributions across the cluster, each multiplied by
+  //    the conjugate of its class twiddle; each block stores one contiguous
+  //    1/CL share of the plane
   if (CL > 1) cluster.sync();
   else __syncthreads();
   const int nout = 3 * g.nz * g.ny;
@@ -271,10 +268,13 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   for (int o = rank * chunk + threadIdx.x; o < o_end; o += NT) {
     const int y = o % g.ny, z = (o / g.ny) % g.nz, c = o / (g.ny * g.nz);
     const int e = c * CS + z * RP + y;
-    float2 v = s[e];
-    for (int q = 1; q < CL; ++q) {
-      const float2* rs = cluster.map_shared_rank(s, (rank + q) % CL);
-      v = cadd(v, rs[e]);
+    const float2 ty = cconj(rty[y]), tz = cconj(rtz[z]), tyz = cmul(ty, tz);
+    float2 v = make_float2(0.f, 0.f);
+    for (int q = 0; q < CL; ++q) {
+      const float2 val = q == rank ? s[e] : cluster.map_shared_rank(s, q)[e];
+      const int qy = q % g.cly, qz = q / g.cly;
+      const float2 w = qy ? (qz ? tyz : ty) : (qz ? tz : make_float2(1.f, 0.f));
+      v = cadd(v, (qy || qz) ? cmul(val, w) : val);
     }
     spec[tidx(g, c, kx, z, y)] = v;
   }
@@ -389,10 +389,23 @@ void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStr
   launch_demag_fused_batch(g, b, m, s, BatchArgs{1, nullptr, nullptr, 0});
 }
 
+static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba);
+
+void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s) {
+  launch_yz_batch(g, b, s, BatchArgs{1, nullptr, nullptr, 0});
+}
+
 void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
 #define CALL_FX(LL) run_fx_t<LL>(g, b, m, s, ba)
   MM_ROWL(g.lx, CALL_FX)
 #undef CALL_FX
+  launch_yz_batch(g, b, s, ba);
+#define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
+  MM_ROWL(g.lx, CALL_IX)
+#undef CALL_IX
+}
+
+static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
   const int key = g.ly * 100 + g.lz;
   switch (key) {
 #define YZ(LY, LZ) \
@@ -406,9 +419,6 @@ void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, c
 #undef YZ
     default: break;
   }
-#define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
-  MM_ROWL(g.lx, CALL_IX)
-#undef CALL_IX
 }
 
 }  // namespace mm

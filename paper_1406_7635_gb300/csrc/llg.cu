@@ -13,122 +13,10 @@
 // runs the controller), so it can be captured once in a CUDA graph and
 // replayed: every launch reads the step size and the buffer roles from
 // DevState, and returns at once when the controller has marked the call done.
-#include <cfloat>
-
-#include "mm_internal.h"
+#include "llg_device.cuh"
 
 namespace mm {
 namespace {
-
-// Dormand & Prince (1980) tableau: nodes, stage weights, 5th-order weights
-// minus embedded 4th-order weights (error estimate).
-__constant__ double kC[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
-__constant__ double kA[7][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5.0, 0, 0, 0, 0, 0},
-    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
-    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
-    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
-    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
-    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
-__constant__ double kE[7] = {71.0 / 57600.0,      0.0,           -71.0 / 16695.0, 71.0 / 1920.0,
-                             -17253.0 / 339200.0, 22.0 / 525.0, -1.0 / 40.0};
-
-// stage coefficients of the current attempt, h * a_sj and h * e_j, in float
-struct StageCoef {
-  float ah[7][6];
-  float eh[7];
-};
-
-__device__ __forceinline__ int k_role(int j, int parity) {
-  // FSAL: after an accepted step the 7th stage becomes the next 1st stage;
-  // instead of copying, buffers 0 and 6 swap roles
-  return j == 0 ? (parity ? 6 : 0) : (j == 6 ? (parity ? 0 : 6) : j);
-}
-
-struct Ptrs {
-  float* m0;
-  float* m1;
-  float* k[7];
-};
-
-__device__ __forceinline__ bool is_magnetic(const uint8_t* __restrict__ mask, const uint8_t* __restrict__ region,
-                                            const RegionLUT* __restrict__ lut, long long i) {
-  return mask[i] != 0 && __ldg(&lut->msat[region[i]]) > 0.0f;
-}
-
-// ----------------------------------------------------------------------------
-// effective field at one cell
-// ----------------------------------------------------------------------------
-struct FieldParts {
-  float3 demag, exch, anis1, anis2, zee;
-};
-
-__device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
-
-__device__ void field_at(const Geom& g, const Buffers& b, const Terms& T, const float* __restrict__ m, long long i,
-                         int x, int y, int z, int r, float3 mi, float sinft, FieldParts& P) {
-  const RegionLUT* __restrict__ lut = b.lut;
-  P.demag = T.demag ? f3(b.bd[i], b.bd[g.n + i], b.bd[2 * g.n + i]) : f3(0, 0, 0);
-  float3 ex = f3(0, 0, 0);
-  if (T.exch) {
-    const float* __restrict__ xl = b.xlut + r * kRegions;
-    auto nb = [&](long long j, float id2) {
-      if (!is_magnetic(b.mask, b.region, lut, j)) return;
-      const float c = __ldg(&xl[b.region[j]]) * id2;
-      ex.x += c * (m[j] - mi.x);
-      ex.y += c * (m[g.n + j] - mi.y);
-      ex.z += c * (m[2 * g.n + j] - mi.z);
-    };
-    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
-    if (x > 0) nb(i - sx, g.idx2);
-    if (x < g.nx - 1) nb(i + sx, g.idx2);
-    if (y > 0) nb(i - sy, g.idy2);
-    if (y < g.ny - 1) nb(i + sy, g.idy2);
-    if (z > 0) nb(i - sz, g.idz2);
-    if (z < g.nz - 1) nb(i + sz, g.idz2);
-  }
-  P.exch = ex;
-  if (T.anis) {
-    const float ux = __ldg(&lut->u[0][r]), uy = __ldg(&lut->u[1][r]), uz = __ldg(&lut->u[2][r]);
-    const float um = ux * mi.x + uy * mi.y + uz * mi.z;
-    const float a1 = __ldg(&lut->k1[r]) * um;
-    const float a2 = __ldg(&lut->k2[r]) * um * um * um;
-    P.anis1 = f3(a1 * ux, a1 * uy, a1 * uz);
-    P.anis2 = f3(a2 * ux, a2 * uy, a2 * uz);
-  } else {
-    P.anis1 = P.anis2 = f3(0, 0, 0);
-  }
-  if (T.zeeman) {
-    P.zee = f3(__ldg(&lut->b0[0][r]) + __ldg(&lut->b1[0][r]) * sinft,
-               __ldg(&lut->b0[1][r]) + __ldg(&lut->b1[1][r]) * sinft,
-               __ldg(&lut->b0[2][r]) + __ldg(&lut->b1[2][r]) * sinft);
-  } else {
-    P.zee = f3(0, 0, 0);
-  }
-}
-
-__device__ __forceinline__ float3 total(const FieldParts& P) {
-  return f3(P.demag.x + P.exch.x + P.anis1.x + P.anis2.x + P.zee.x,
-            P.demag.y + P.exch.y + P.anis1.y + P.anis2.y + P.zee.y,
-            P.demag.z + P.exch.z + P.anis1.z + P.anis2.z + P.zee.z);
-}
-
-__device__ __forceinline__ float3 llg_torque(float3 m, float3 B, float gfac, float alpha, int precession) {
-  const float3 mxB = f3(m.y * B.z - m.z * B.y, m.z * B.x - m.x * B.z, m.x * B.y - m.y * B.x);
-  const float3 mxmxB = f3(m.y * mxB.z - m.z * mxB.y, m.z * mxB.x - m.x * mxB.z, m.x * mxB.y - m.y * mxB.x);
-  const float p = precession ? 1.0f : 0.0f;
-  return f3(gfac * (p * mxB.x + alpha * mxmxB.x), gfac * (p * mxB.y + alpha * mxmxB.y),
-            gfac * (p * mxB.z + alpha * mxmxB.z));
-}
-
-// sin(2 pi f t + phase), with the phase reduced in float64 before a float
-// sinpi (one function of time for the whole excitation)
-__device__ __forceinline__ float excitation(double f, double phase_over_pi, double t) {
-  double y = 2.0 * (f * t - floor(f * t)) + phase_over_pi;
-  y -= 2.0 * floor(0.5 * y);
-  return sinpif((float)y);
-}
 
 // ----------------------------------------------------------------------------
 // kernels
@@ -144,7 +32,7 @@ __global__ void k_stage_input(Geom g, Ptrs p, float* __restrict__ ms, const DevS
   for (int j = 0; j < s; ++j) {
     const float a = sc->ah[s][j];
     if (a == 0.0f) continue;
-    const float* __restrict__ k = p.k[k_role(j, par)];
+    const float* __restrict__ k = pick_k(p, k_role(j, par));
     acc[0] = fmaf(a, k[i], acc[0]);
     acc[1] = fmaf(a, k[g.n + i], acc[1]);
     acc[2] = fmaf(a, k[2 * g.n + i], acc[2]);
@@ -161,7 +49,7 @@ __global__ void k_torque(Geom g, Buffers b, Terms T, Ptrs p, const DevState* __r
   if (i >= g.n) return;
   const int par = st->parity;
   const float* __restrict__ m = s == 0 ? (par ? p.m1 : p.m0) : b.ms;
-  float* __restrict__ k = p.k[k_role(s, par)];
+  float* __restrict__ k = pick_k(p, k_role(s, par));
   const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
   const int r = b.region[i];
   if (!(b.mask[i] && b.lut->msat[r] > 0.0f)) {
@@ -171,31 +59,11 @@ __global__ void k_torque(Geom g, Buffers b, Terms T, Ptrs p, const DevState* __r
   const float3 mi = f3(m[i], m[g.n + i], m[2 * g.n + i]);
   const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->stage_t[s]) : 0.0f;
   FieldParts P;
-  field_at(g, b, T, m, i, x, y, z, r, mi, sinft, P);
+  field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[g.n + i], b.bd[2 * g.n + i]), P);
   const float3 tq = llg_torque(mi, total(P), b.lut->gfac[r], b.lut->alpha[r], st->precession);
   k[i] = tq.x;
   k[g.n + i] = tq.y;
   k[2 * g.n + i] = tq.z;
-}
-
-// per-attempt set-up: step size, stage times, stage coefficients
-__device__ void prepare_attempt(DevState* st, StageCoef* sc, const double* __restrict__ fixed) {
-  double h;
-  if (st->mode == 2) h = fixed[st->fixed_idx];
-  else if (st->mode == 1) h = fmin(st->dt, st->t_end - st->t);
-  else h = st->dt;
-  st->h = h;
-  for (int s = 0; s < 7; ++s) {
-    st->stage_t[s] = st->t + kC[s] * h;
-    for (int j = 0; j < 6; ++j) sc->ah[s][j] = (float)(kA[s][j] * h);
-    sc->eh[s] = (float)(kE[s] * h);
-  }
-}
-
-__device__ void check_done(DevState* st) {
-  if (st->mode == 0 && st->accepted >= st->target) st->done = 1;
-  if (st->mode == 1 && st->t >= st->t_end) st->done = 1;
-  if (st->mode == 2 && (st->fixed_idx >= st->fixed_n || st->accepted >= st->target)) st->done = 1;
 }
 
 __global__ void k_begin(DevState* st, StageCoef* sc, const double* __restrict__ fixed, int mode, long long nsteps,
@@ -214,51 +82,6 @@ __global__ void k_begin(DevState* st, StageCoef* sc, const double* __restrict__ 
   if (!st->done) prepare_attempt(st, sc, fixed);
 }
 
-// The controller (Sec. IV, "Adaptive time step"): eps = max |tau_5 - tau_4| dt
-// against MaxErr with headroom 0.8.  Readings: accept iff eps <= MaxErr;
-// dt_new = dt clamp(0.8 (MaxErr/eps)^(1/5), 0.2, 5), bounded by dt_max, and
-// at least dt_min after an accepted step; a rejection that would need a step
-// below dt_min ends the call with MM_ERR_DT_UNDERFLOW.
-__device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ hist,
-                           const double* __restrict__ fixed) {
-  const double eps = (double)__uint_as_float(st->err_bits);
-  st->err_bits = 0;
-  st->ticket = 0;
-  st->evals += 6;
-  st->call_attempts++;
-  st->last_err = eps;
-  if (!(eps <= DBL_MAX)) {
-    st->status = -4;   // MM_ERR_NONFINITE
-    st->done = 1;
-    return;
-  }
-  const double h = st->h;
-  const bool replay = st->mode == 2;
-  const bool accept = replay || eps <= st->max_err;
-  const double factor = eps == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, st->headroom * pow(st->max_err / eps, 0.2)));
-  const double ndt = fmin(h * factor, st->dt_max);
-  if (accept) {
-    st->t += h;
-    if (st->mode == 1 && st->t + 1e-6 * h >= st->t_end) st->t = st->t_end;
-    st->parity ^= 1;
-    if (st->hist_n < kHistCap) hist[st->hist_n] = h;
-    st->hist_n++;
-    st->accepted++;
-    if (replay) st->fixed_idx++;
-    else st->dt = fmax(ndt, st->dt_min);
-    check_done(st);
-  } else {
-    st->rejected++;
-    if (ndt < st->dt_min) {
-      st->status = -5;   // MM_ERR_DT_UNDERFLOW
-      st->done = 1;
-      return;
-    }
-    st->dt = ndt;
-  }
-  if (!st->done) prepare_attempt(st, sc, fixed);
-}
-
 // error estimate, candidate m (normalised 5th-order solution), block max,
 // controller in the last block
 __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict__ st, StageCoef* __restrict__ sc) {
@@ -274,7 +97,7 @@ __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict_
       for (int j = 0; j < 7; ++j) {
         const float c = sc->eh[j];
         if (c == 0.0f) continue;
-        const float* __restrict__ k = p.k[k_role(j, par)];
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
         ex = fmaf(c, k[i], ex);
         ey = fmaf(c, k[g.n + i], ey);
         ez = fmaf(c, k[2 * g.n + i], ez);
@@ -326,7 +149,7 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
       const float3 mi = f3(m[i], m[g.n + i], m[2 * g.n + i]);
       const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->t) : 0.0f;
       FieldParts P;
-      field_at(g, b, T, m, i, x, y, z, r, mi, sinft, P);
+      field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[g.n + i], b.bd[2 * g.n + i]), P);
       const float3 B = total(P);
       if (mode == 0) out = B;
       else if (mode == 1) out = llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession);

@@ -159,8 +159,19 @@ void enqueue_demag(mm_ctx* c) {
     launch_demag(c->g, c->b, c->b.ms, c->stream);
 }
 
+// The row-stage path (fused convolution layout, exact demag): per attempt one
+// prep kernel, then per stage the (y, z) transform and one row kernel.
+bool rowstage_path(const mm_ctx* c) { return c->g.fused && !c->sur_active; }
+
 // stage-1 torque at the current m (FSAL start)
 void enqueue_k1(mm_ctx* c) {
+  if (rowstage_path(c)) {
+    c->launches += 2 + (c->T.demag ? 1 : 0);
+    launch_rowstage(c->g, c->b, c->T, 0, 0, 0, c->freq, c->phase, c->stream);
+    if (c->T.demag) launch_demag_yz(c->g, c->b, c->stream);
+    launch_rowstage(c->g, c->b, c->T, 1, 0, 0, c->freq, c->phase, c->stream);
+    return;
+  }
   c->launches += 2 + (c->T.demag ? demag_launches(c->g) : 0);
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
   enqueue_demag(c);
@@ -168,6 +179,14 @@ void enqueue_k1(mm_ctx* c) {
 }
 
 void enqueue_attempt(mm_ctx* c) {
+  if (rowstage_path(c)) {
+    launch_rowstage(c->g, c->b, c->T, 0, 1, 0, c->freq, c->phase, c->stream);
+    for (int s = 1; s < 7; ++s) {
+      if (c->T.demag) launch_demag_yz(c->g, c->b, c->stream);
+      launch_rowstage(c->g, c->b, c->T, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
+    }
+    return;
+  }
   for (int s = 1; s < 7; ++s) {
     launch_stage_input(c->g, c->b, s, c->stream);
     enqueue_demag(c);
@@ -336,6 +355,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   alloc((void**)&b.m[1], vec);
   for (int j = 0; j < 7; ++j) alloc((void**)&b.k[j], vec);
   alloc((void**)&b.ms, vec);
+  if (g.fused) alloc((void**)&b.ms2, vec);
   alloc((void**)&b.bd, vec);
   alloc((void**)&b.out, vec);
   alloc((void**)&b.spec, 3 * (size_t)g.sc * sizeof(float2));
@@ -403,7 +423,7 @@ int mm_destroy(mm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   Buffers& b = c->b;
-  void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.bd, b.out,
+  void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.ms2, b.bd, b.out,
                   b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed,
                   c->sur_acc};
   for (void* p : ptrs)

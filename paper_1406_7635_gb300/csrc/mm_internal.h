@@ -65,7 +65,8 @@ struct DevState {
 struct Buffers {
   float* m[2];        // current / candidate m (parity)
   float* k[7];        // RK stages; k[0] and k[6] swap roles with parity
-  float* ms;          // stage input m_s
+  float* ms;          // stage input m_s (even stages of the row-stage path)
+  float* ms2;         // odd-stage inputs of the row-stage path
   float* bd;          // demag field
   float2* spec;       // spectrum work buffer
   float* kt;          // kernel spectrum octant [6][hkz][hky][hkx]
@@ -110,6 +111,13 @@ bool fused_plan(Geom& g);
 void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
 void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba);
 void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s);
+// only the (y, z) part of the fused convolution (k_yz), spectrum in place
+void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s);
+// fused RK45 stage kernels (rowstage.cu): kind 0 = stage-input prep of stage
+// s, kind 1 = row kernel of stage s (mode 0 first stage only, 1 next stage,
+// 2 last stage with error and controller)
+void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
+                     double phase, cudaStream_t st);
 // kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
                                   cudaStream_t s);

@@ -1,0 +1,341 @@
+// Fused RK45 stage kernels for the fused convolution layout (spec as
+// [c][kx][z][y]): per attempt, one prep kernel and, per stage, k_yz plus one
+// row kernel, instead of five kernels per stage.
+//
+// A block owns ROWS complete x-rows (one z plane) of all three components.
+//   k_rs_prep  stage input m_s = m + dt sum_j a_sj k_j for its cells, written
+//              for the neighbours' stencils, then M = Msat m_s -> x R2C into
+//              the spectrum rows it owns;
+//   k_rs_row   x C2R of the demag spectrum of stage s (B_demag stays in
+//              shared memory) -> effective field and LL torque k_s of its
+//              cells -> next stage input m_{s+1} and its x R2C, or, after the
+//              last stage, the error estimate, the candidate m and (last
+//              block) the step controller (Sec. IV).
+// Stage inputs alternate between two buffers (ms for even stages, ms2 for odd
+// ones), because a stage's stencil reads neighbours owned by other blocks.
+#include "fft.cuh"
+#include "llg_device.cuh"
+
+namespace mm {
+namespace {
+using namespace mmfft;
+
+enum { ROW_K1 = 0, ROW_NEXT = 1, ROW_LAST = 2 };
+
+__device__ __forceinline__ float* stage_buf(const Buffers& b, int s) { return (s & 1) ? b.ms2 : b.ms; }
+
+__device__ __forceinline__ long long tix(const Geom& g, int c, int kx, int z, int y) {
+  return (((long long)c * g.hx + kx) * g.nz + z) * g.ny + y;
+}
+
+// x R2C of the packed rows in s (3 * ROWS pencils) into the spectrum
+template <int L, int ROWS, int NT>
+__device__ __forceinline__ void rows_fx(const Geom& g, float2* s, const float2* twl, const float2* tw2, float2* spec,
+                                        int y0, int z) {
+  constexpr int PST = L + 1;
+  FftG<L, -1, 3 * ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
+    const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
+    const int y = y0 + r;
+    if (y >= g.ny) continue;
+    const float2* row = s + (c * ROWS + r) * PST;
+    const float2 zk = row[k & (L - 1)];
+    const float2 zc = cconj(row[(L - k) & (L - 1)]);
+    const float2 E = cscale(cadd(zk, zc), 0.5f);
+    const float2 d = csub(zk, zc);
+    const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);
+    spec[tix(g, c, k, z, y)] = cadd(E, cmul(tw2[k], O));
+  }
+}
+
+template <int L, int NT>
+__device__ __forceinline__ void load_tables(float2* twl, float2* tw2, const float2* __restrict__ tw) {
+  load_twiddles<L, NT>(twl, tw);
+  for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
+}
+
+template <int L, int ROWS, int NT>
+__global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const DevState* __restrict__ st,
+                                               const StageCoef* __restrict__ sc, int s) {
+  if (st->done) return;
+  constexpr int PST = L + 1;
+  __shared__ float2 sm[3 * ROWS * PST];
+  __shared__ float2 twl[L], tw2[L + 1];
+  const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
+  load_tables<L, NT>(twl, tw2, b.tw);
+  float* sf = reinterpret_cast<float*>(sm);
+  const int par = st->parity;
+  const float* __restrict__ m = par ? p.m1 : p.m0;
+  float* __restrict__ out = stage_buf(b, s);
+  for (int e = threadIdx.x; e < ROWS * 2 * L; e += NT) {
+    const int x = e % (2 * L), r = e / (2 * L), y = y0 + r;
+    float v[3] = {0.f, 0.f, 0.f};
+    if (y < g.ny && x < g.nx) {
+      const long long i = ((long long)z * g.ny + y) * g.nx + x;
+      float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
+      for (int j = 0; j < s; ++j) {
+        const float a = sc->ah[s][j];
+        if (a == 0.0f) continue;
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
+        a0 = fmaf(a, k[i], a0);
+        a1 = fmaf(a, k[g.n + i], a1);
+        a2 = fmaf(a, k[2 * g.n + i], a2);
+      }
+      out[i] = a0;
+      out[g.n + i] = a1;
+      out[2 * g.n + i] = a2;
+      const float ms = is_magnetic(b.mask, b.region, b.lut, i) ? __ldg(&b.lut->msat[b.region[i]]) : 0.f;
+      v[0] = ms * a0;
+      v[1] = ms * a1;
+      v[2] = ms * a2;
+    }
+    for (int c = 0; c < 3; ++c) sf[2 * (c * ROWS + r) * PST + x] = v[c];
+  }
+  __syncthreads();
+  rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
+}
+
+template <int L, int ROWS, int NT>
+__global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Ptrs p, DevState* __restrict__ st,
+                                                 StageCoef* __restrict__ sc, int s, int mode, double freq,
+                                                 double phase_over_pi) {
+  if (st->done) return;   // uniform: the controller runs after every block of this launch
+  constexpr int PST = L + 1;
+  // real cells per thread: ROWS rows of at most L cells (nx <= 2L, and the
+  // x-padding cells are not visited)
+  constexpr int CPT = (ROWS * L + NT - 1) / NT;
+  __shared__ float2 sm[3 * ROWS * PST];
+  __shared__ float2 twl[L], tw2[L + 1];
+  __shared__ float wmax[32];
+  const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
+  load_tables<L, NT>(twl, tw2, b.tw);
+  // 1. x C2R of the demag spectrum rows (3 components)
+  for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
+    const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
+    const int y = y0 + r;
+    sm[(c * ROWS + r) * PST + k] = y < g.ny ? b.spec[tix(g, c, k, z, y)] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
+    const int pen = e / (L / 2 + 1), k = e % (L / 2 + 1);
+    float2* row = sm + pen * PST;
+    const float2 xa = row[k], xb = row[L - k];
+    float2 za, zb;
+    {
+      const float2 E = cscale(cadd(xa, cconj(xb)), 0.5f);
+      const float2 O = cmul(cscale(csub(xa, cconj(xb)), 0.5f), cconj(tw2[k]));
+      za = make_float2(E.x - O.y, E.y + O.x);
+    }
+    {
+      const float2 E = cscale(cadd(xb, cconj(xa)), 0.5f);
+      const float2 O = cmul(cscale(csub(xb, cconj(xa)), 0.5f), cconj(tw2[L - k]));
+      zb = make_float2(E.x - O.y, E.y + O.x);
+    }
+    row[k] = za;
+    if (k != 0 && k != L / 2) row[L - k] = zb;
+  }
+  __syncthreads();
+  FftG<L, 1, 3 * ROWS, NT, 1, PST, 1, L>::run(sm, twl);
+  // 2. field and torque of the block's cells
+  const float* sf = reinterpret_cast<const float*>(sm);
+  const int par = st->parity;
+  const float* __restrict__ ms = stage_buf(b, s);
+  float* __restrict__ kout = pick_k(p, k_role(s, par));
+  const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->stage_t[s]) : 0.0f;
+  // each thread's cells: e = tid + q NT over the ROWS x nx real cells
+  const int ncell = ROWS * g.nx;
+  float kv[CPT][3];
+  bool magv[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int e = threadIdx.x + q * NT;
+    kv[q][0] = kv[q][1] = kv[q][2] = 0.f;
+    magv[q] = false;
+    if (e >= ncell) continue;
+    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
+    if (y >= g.ny) continue;
+    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    const int reg = b.region[i];
+    if (b.mask[i] && b.lut->msat[reg] > 0.0f) {
+      magv[q] = true;
+      const float3 mi = f3(ms[i], ms[g.n + i], ms[2 * g.n + i]);
+      const float3 bdem = f3(sf[2 * (0 * ROWS + r) * PST + x], sf[2 * (1 * ROWS + r) * PST + x],
+                             sf[2 * (2 * ROWS + r) * PST + x]);
+      FieldParts P;
+      field_at(g, b, T, ms, i, x, y, z, reg, mi, sinft, bdem, P);
+      const float3 tq = llg_torque(mi, total(P), b.lut->gfac[reg], b.lut->alpha[reg], st->precession);
+      kv[q][0] = tq.x;
+      kv[q][1] = tq.y;
+      kv[q][2] = tq.z;
+    }
+  }
+  // stores after all loads of the block's cells were issued
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int e = threadIdx.x + q * NT;
+    if (e >= ncell) continue;
+    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
+    if (y >= g.ny) continue;
+    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    kout[i] = kv[q][0];
+    kout[g.n + i] = kv[q][1];
+    kout[2 * g.n + i] = kv[q][2];
+  }
+  if (mode == ROW_K1) return;
+  const float* __restrict__ m = par ? p.m1 : p.m0;
+  if (mode == ROW_NEXT) {
+    // 3. next stage input and its x R2C
+    __syncthreads();   // every thread is done reading B_demag from sm
+    float* sw = reinterpret_cast<float*>(sm);
+    float* __restrict__ nxt = stage_buf(b, s + 1);
+    // x padding (x >= nx) and rows past the grid are zero
+    for (int e = threadIdx.x; e < 3 * ROWS * 2 * L; e += NT) {
+      const int x = e % (2 * L), row = e / (2 * L), r = row % ROWS;
+      if (x >= g.nx || y0 + r >= g.ny) sw[2 * row * PST + x] = 0.f;
+    }
+    float nv[CPT][3];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int e = threadIdx.x + q * NT;
+      nv[q][0] = nv[q][1] = nv[q][2] = 0.f;
+      if (e >= ncell) continue;
+      const int x = e % g.nx, r = e / g.nx, y = y0 + r;
+      if (y >= g.ny) continue;
+      const long long i = ((long long)z * g.ny + y) * g.nx + x;
+      float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
+      for (int j = 0; j < s; ++j) {
+        const float a = sc->ah[s + 1][j];
+        if (a == 0.0f) continue;
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
+        a0 = fmaf(a, k[i], a0);
+        a1 = fmaf(a, k[g.n + i], a1);
+        a2 = fmaf(a, k[2 * g.n + i], a2);
+      }
+      const float a = sc->ah[s + 1][s];
+      nv[q][0] = fmaf(a, kv[q][0], a0);
+      nv[q][1] = fmaf(a, kv[q][1], a1);
+      nv[q][2] = fmaf(a, kv[q][2], a2);
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e >= ncell) continue;
+      const int x = e % g.nx, r = e / g.nx, y = y0 + r;
+      if (y >= g.ny) continue;
+      const long long i = ((long long)z * g.ny + y) * g.nx + x;
+      nxt[i] = nv[q][0];
+      nxt[g.n + i] = nv[q][1];
+      nxt[2 * g.n + i] = nv[q][2];
+      const float msat = magv[q] ? __ldg(&b.lut->msat[b.region[i]]) : 0.f;
+      for (int c = 0; c < 3; ++c) sw[2 * (c * ROWS + r) * PST + x] = msat * nv[q][c];
+    }
+    __syncthreads();
+    rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
+    return;
+  }
+  // 3'. last stage: error estimate, candidate m, block max, controller
+  float emax = 0.f;
+  float* __restrict__ mnew = par ? p.m0 : p.m1;
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int e = threadIdx.x + q * NT;
+    if (e >= ncell) continue;
+    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
+    if (y >= g.ny) continue;
+    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    if (magv[q]) {
+      float ex = sc->eh[6] * kv[q][0], ey = sc->eh[6] * kv[q][1], ez = sc->eh[6] * kv[q][2];
+      for (int j = 0; j < 6; ++j) {
+        const float c = sc->eh[j];
+        if (c == 0.0f) continue;
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
+        ex = fmaf(c, k[i], ex);
+        ey = fmaf(c, k[g.n + i], ey);
+        ez = fmaf(c, k[2 * g.n + i], ez);
+      }
+      float err = sqrtf(ex * ex + ey * ey + ez * ez);
+      if (!(err <= FLT_MAX)) err = __int_as_float(0x7f800000);
+      emax = fmaxf(emax, err);
+      const float mx = ms[i], my = ms[g.n + i], mz = ms[2 * g.n + i];
+      const float inv = rsqrtf(mx * mx + my * my + mz * mz);
+      mnew[i] = mx * inv;
+      mnew[g.n + i] = my * inv;
+      mnew[2 * g.n + i] = mz * inv;
+    } else {
+      mnew[i] = mnew[g.n + i] = mnew[2 * g.n + i] = 0.0f;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (NT >> 5) ? wmax[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) {
+      atomicMax(&st->err_bits, __float_as_uint(v));
+      __threadfence();
+      const unsigned int t = atomicAdd(&st->ticket, 1u);
+      if (t == gridDim.x * gridDim.y - 1) {
+        __threadfence();
+        controller(st, sc, b.hist, b.fixed);
+      }
+    }
+  }
+}
+
+Ptrs rs_ptrs(const Buffers& b) {
+  Ptrs p;
+  p.m0 = b.m[0];
+  p.m1 = b.m[1];
+  for (int j = 0; j < 7; ++j) p.k[j] = b.k[j];
+  return p;
+}
+
+// ROWS * L = 1024 points per block, or 256 when that leaves too few blocks
+template <int L, int ROWS>
+struct RsCfg {
+  static constexpr int NT0 = 3 * ROWS * L / 8;
+  static constexpr int NT = NT0 < 64 ? 64 : (NT0 > 512 ? 512 : NT0);
+};
+
+template <int L, int ROWS>
+void launch_rs(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq, double phase,
+               cudaStream_t st) {
+  using C = RsCfg<L, ROWS>;
+  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz);
+  StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
+  if (kind == 0)
+    k_rs_prep<L, ROWS, C::NT><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s);
+  else
+    k_rs_row<L, ROWS, C::NT><<<grid, C::NT, 0, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq,
+                                                      phase / 3.14159265358979323846);
+}
+
+template <int L>
+void launch_rs_l(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
+                 double phase, cudaStream_t st) {
+  constexpr int R1 = L >= 1024 ? 1 : 1024 / L;
+  constexpr int R2 = L >= 256 ? 1 : 256 / L;
+  const long long blocks1 = (long long)((g.ny + R1 - 1) / R1) * g.nz;
+  if (blocks1 >= 300) launch_rs<L, R1>(g, b, T, kind, s, mode, freq, phase, st);
+  else launch_rs<L, R2>(g, b, T, kind, s, mode, freq, phase, st);
+}
+
+}  // namespace
+
+// kind 0: prep of stage s; kind 1: row kernel of stage s with mode 0 (first
+// stage only), 1 (next stage), 2 (last stage: error and controller)
+void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
+                     double phase, cudaStream_t st) {
+  switch (g.lx) {
+    case 16: launch_rs_l<16>(g, b, T, kind, s, mode, freq, phase, st); break;
+    case 32: launch_rs_l<32>(g, b, T, kind, s, mode, freq, phase, st); break;
+    case 64: launch_rs_l<64>(g, b, T, kind, s, mode, freq, phase, st); break;
+    case 128: launch_rs_l<128>(g, b, T, kind, s, mode, freq, phase, st); break;
+    case 256: launch_rs_l<256>(g, b, T, kind, s, mode, freq, phase, st); break;
+    case 512: launch_rs_l<512>(g, b, T, kind, s, mode, freq, phase, st); break;
+    default: break;
+  }
+}
+
+}  // namespace mm

@@ -186,10 +186,24 @@ def ellipsoid_vortex(nx=128, ny=128, nz=32, c=3e-9, seed=SEED_BASE + 2):
     return p
 
 
+def film_surrogate(nx=512, ny=512, seed=SEED_BASE + 4):
+    """Film of nx x ny x 1 cells of 2 x 2 x 2 nm for the learned demag
+    surrogate: Msat 8e5 A/m, Aex 1.3e-11 J/m, alpha 0.02, no anisotropy, a
+    static 20 mT field along (1, 1, 0)/sqrt 2; m0 uniform on the sphere."""
+    rng = np.random.default_rng(seed)
+    p = Problem(nx, ny, 1, 2e-9, 2e-9, 2e-9)
+    p.msat[0], p.aex[0], p.alpha[0] = 8e5, 1.3e-11, 0.02
+    p.anis = False
+    p.b0[0] = (20e-3 / np.sqrt(2.0), 20e-3 / np.sqrt(2.0), 0.0)
+    p.m0 = normalise(random_unit(rng, p.shape), p.magnetic())
+    return p
+
+
 WORKLOADS = {
     "film_64x16x1": lambda: film_sp4(64, 16),
     "grains_256x256x1": lambda: grain_film(256, 256, 64),
     "ellipsoid_128x128x32": lambda: ellipsoid_vortex(128, 128, 32),
+    "film_512x512x1": lambda: film_surrogate(512, 512),
 }
 
 
