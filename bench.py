@@ -102,14 +102,90 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _pad(n):
+    return 1 if n == 1 else 1 << (2 * n - 2).bit_length()
+
+
 def algorithmic_demag_bytes(p):
-    """Minimum HBM bytes of one demag convolution: read m (3 x 4 B) and the
-    mask/region bytes (2 B) per cell, the kernel spectrum octant (6 float32 per
-    octant point), write B (3 x 4 B) per cell."""
+    """Minimum HBM bytes of one demag convolution (50 B per cell at 128 x 128
+    x 32): read m (3 x 4 B) and the mask/region bytes (2 B) per cell, the
+    kernel spectrum octant (6 float32 per octant point), write B (3 x 4 B)
+    per cell."""
     def half(n):
-        return 1 if n == 1 else (1 << (2 * n - 2).bit_length()) // 2 + 1
+        return 1 if n == 1 else _pad(n) // 2 + 1
     octant = half(p.nx) * half(p.ny) * half(p.nz)
     return p.ncells * (12 + 2 + 12) + 6 * 4 * octant
+
+
+def five_pass_demag_bytes(p):
+    """HBM bytes of the unfused five-pass design (x R2C, y, z*K*z^-1, y^-1,
+    x C2R, each pass through memory, pruned to the rows that carry data):
+    340 B per cell at 128 x 128 x 32."""
+    px, py, pz = _pad(p.nx), _pad(p.ny), _pad(p.nz)
+    hx = px // 2 + 1 if px > 1 else 1
+    c8 = 3 * 8
+    x_out = c8 * hx * p.ny * p.nz
+    y_out = c8 * hx * py * p.nz
+    pass1 = p.ncells * (12 + 2) + x_out
+    kern = algorithmic_demag_bytes(p) - p.ncells * 26
+    if pz == 1:                                   # 2-D: y*K*y^-1 is one pass
+        return pass1 + 2 * x_out + kern + x_out + 12 * p.ncells
+    pass2 = x_out + y_out
+    pass3 = 2 * y_out + kern                      # z pruned both ways, + kernel
+    pass4 = y_out + x_out
+    pass5 = x_out + 12 * p.ncells
+    return pass1 + pass2 + pass3 + pass4 + pass5
+
+
+def algorithmic_demag_flops(p):
+    """Floating-point operations of one demag convolution, counted as 5 L
+    log2 L per complex transform of length L and 2.5 L log2 L per real one,
+    over the lines that carry data (x: ny*nz rows per component, y: hx*nz
+    columns, z: hx*py columns), forward and inverse, plus the spectral
+    product (30 flops per frequency point in 3-D, 14 in 2-D where Kxz = Kyz
+    = 0).  823 MFLOP at 128 x 128 x 32."""
+    from math import log2
+    px, py, pz = _pad(p.nx), _pad(p.ny), _pad(p.nz)
+    hx = px // 2 + 1 if px > 1 else 1
+    f = 0.0
+    if px > 1:
+        f += 2 * 3 * p.ny * p.nz * 2.5 * px * log2(px)
+    if py > 1:
+        f += 2 * 3 * hx * p.nz * 5 * py * log2(py)
+    if pz > 1:
+        f += 2 * 3 * hx * py * 5 * pz * log2(pz)
+    f += (30 if pz > 1 else 14) * hx * py * pz
+    return f
+
+
+# FP32 issue peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x
+# 2.070 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+CONV_SOURCES = ("paper_1406_7635_gb300/csrc/fft_fused.cu", "paper_1406_7635_gb300/csrc/fft.cuh")
+
+
+def conv_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in CONV_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def conv_traffic(workload):
+    """DRAM bytes of one convolution from the committed ncu summary of the
+    same workload, or None when the convolution's sources changed since the
+    counters were taken."""
+    prof = os.path.join(ROOT, "profiles", f"demag_conv_{workload}.json")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        d = json.load(f)
+    if d.get("src_sha256_16") != conv_sources_sha():
+        return None
+    return d.get("dram_bytes_per_conv")
 
 
 def run_ours(args, rank, world, local_rank):
@@ -186,16 +262,21 @@ def run_ours(args, rank, world, local_rank):
     conv_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / R
     peaks, peak_kind = measured_peaks()
     alg = algorithmic_demag_bytes(p)
-    achieved = alg / conv_s / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", f"demag_conv_{args.workload}.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            traffic = json.load(f).get("dram_bytes_per_conv")
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                "kernel": "demag FFT convolution (x R2C, y, z*K*z^-1, y^-1, x C2R passes)",
-                "algorithmic_bytes": alg, "avg_launch_us": round(conv_s * 1e6, 2), "peak_kind": peak_kind}
+    flops = algorithmic_demag_flops(p)
+    achieved = flops / conv_s / 1e12
+    floor_gbs = alg / conv_s / 1e9
+    five_gbs = five_pass_demag_bytes(p) / conv_s / 1e9
+    roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": conv_traffic(args.workload),
+                "kernel": "demag FFT convolution (x R2C, fused y/z*K*z^-1/y^-1 cluster kernel, x C2R)",
+                "algorithmic_flops": flops, "avg_launch_us": round(conv_s * 1e6, 2),
+                "peak_kind": "derived FP32 issue peak (152 SM x 128 lanes x FMA x 2.07 GHz)",
+                "hbm": {"peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+                        "floor_bytes": alg, "floor_gbs": round(floor_gbs, 1),
+                        "floor_frac": round(floor_gbs / peaks["hbm_gbs"], 4),
+                        "five_pass_bytes": five_pass_demag_bytes(p), "five_pass_equiv_gbs": round(five_gbs, 1),
+                        "five_pass_equiv_frac": round(five_gbs / peaks["hbm_gbs"], 4)}}
 
     # end to end through the C ABI with host buffers: m up, one step, m down
     Ke = min(K, 50)
@@ -235,6 +316,8 @@ def run_ours(args, rank, world, local_rank):
         out["film"] = side
     if args.batch:
         out["batch"] = run_batch(args, local_rank)
+    if args.surrogate:
+        out["surrogate"] = run_surrogate(args, local_rank)
     return out
 
 
@@ -290,6 +373,57 @@ def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
             "sequential_sample": f"{seq_per_shape} instances per grid size, same t_end, extrapolated by count"}
 
 
+def run_surrogate(args, local_rank, steps=40):
+    """The learned demag surrogate on the 512 x 512 x 1 film: trained on
+    args.pairs (m, B_demag) pairs from the context's own exact trajectories,
+    then `steps` RK45 steps timed with the exact convolution, with the guarded
+    surrogate (exact check every 10 steps, fallback above 1e-3) and with the
+    surrogate unguarded."""
+    import torch
+    from paper_1406_7635_gb300 import mm
+    p = WORKLOADS["film_512x512x1"]()
+    net = mm.FNO(p.ny, p.nx, width=32, layers=4, modes_x=24, modes_y=24, max_batch=4, seed=1)
+    ctx = mm.Context.from_problem(p, device=local_rank)
+    t0 = time.perf_counter()
+    loss = ctx.train_surrogate(net, p.msat[0], n_pairs=args.pairs, traj_len=16, steps_between=5,
+                               field_max=50e-3, epochs=args.epochs, batch=4, lr=1e-3, seed=2)
+    train_s = time.perf_counter() - t0
+    ctx.close()
+
+    def timed(setup):
+        c = mm.Context.from_problem(p, device=local_rank)
+        setup(c)
+        c.step(2)                                  # warm-up
+        c.set_m(p.m0)
+        c.set_time(0.0, p.dt0)
+        if setup is not plain:
+            setup(c)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        c.step(steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - ts
+        out = (c.get_m().astype(np.float64), p.ncells * steps / dt, c.surrogate_stats())
+        c.close()
+        return out
+
+    def plain(c):
+        pass
+    m_exact, v_exact, _ = timed(plain)
+    m_guard, v_guard, st_guard = timed(lambda c: c.set_demag_surrogate(net, p.msat[0], 10, 1e-3))
+    m_free, v_free, st_free = timed(lambda c: c.set_demag_surrogate(net, p.msat[0], 10, 1e30))
+    net.close()
+    return {"workload": "film_512x512x1 (2 nm cells), FNO width 32, 4 layers, 24 modes per axis",
+            "pairs": args.pairs, "epochs": args.epochs, "train_s": train_s, "final_train_loss": loss,
+            "steps": steps, "exact_cell_steps_per_s": v_exact,
+            "guarded_cell_steps_per_s": v_guard, "guarded_speedup": v_guard / v_exact,
+            "guard": {k: st_guard[k] for k in ("checks", "fallbacks", "last_rel_err", "steps")},
+            "unguarded_cell_steps_per_s": v_free, "unguarded_speedup": v_free / v_exact,
+            "unguarded_field_rel_err_at_checks": st_free["last_rel_err"],
+            "unguarded_final_m_max_err_vs_exact": float(np.abs(m_free - m_exact).max()),
+            "guarded_final_m_max_err_vs_exact": float(np.abs(m_guard - m_exact).max())}
+
+
 def oracle_cpu_run(name, budget_s, max_steps):
     """The float64 oracle on the same workload: kernel set-up untimed, then
     accepted adaptive RK45 steps until the time budget is spent."""
@@ -337,6 +471,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", dest="side", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-surrogate", dest="surrogate", action="store_false")
+    ap.add_argument("--pairs", type=int, default=256, help="surrogate training pairs (the full recipe: 20000)")
+    ap.add_argument("--epochs", type=int, default=2, help="surrogate training epochs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = env_rank()

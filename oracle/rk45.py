@@ -47,7 +47,15 @@ class NonFinite(RuntimeError):
 
 
 class RK45:
-    """Integrates dm/dt = tau(m, t) from the problem's m0 at t = 0."""
+    """Integrates dm/dt = tau(m, t) from the problem's m0 at t = 0.
+
+    The tableau is read from the class attributes (nodes C, stage rows A,
+    error weights E = b_high - b_low, step-factor exponent 1/(q+1) for an
+    error estimate of order q), so that an embedded pair with the same
+    FSAL structure only overrides them."""
+
+    C, A, E = C, A, E
+    EXPONENT = 0.2
 
     def __init__(self, p, demag_method="fft", m=None):
         self.p = p
@@ -68,19 +76,19 @@ class RK45:
         if self.k1 is None:
             self.k1 = tau(self.m, self.t)
         k = [self.k1]
-        for s in range(1, 7):
+        for s in range(1, len(self.C)):
             ys = self.m.copy()
-            for j, a in enumerate(A[s]):
+            for j, a in enumerate(self.A[s]):
                 if a != 0:
                     ys = ys + h * float(a) * k[j]
-            k.append(tau(ys, self.t + float(C[s]) * h))
-        y_new = ys                      # stage 7 point equals the 5th-order solution
+            k.append(tau(ys, self.t + float(self.C[s]) * h))
+        y_new = ys                      # the last stage point is the high-order solution
         err = np.zeros_like(self.m)
-        for j, e in enumerate(E):
+        for j, e in enumerate(self.E):
             err = err + h * float(e) * k[j]
         norm = np.sqrt((err * err).sum(axis=0))
         eps = float(norm[self.mag].max()) if self.mag.any() else 0.0
-        return y_new, k[6], eps
+        return y_new, k[-1], eps
 
     def _accept(self, y_new, k7, h):
         n = np.sqrt((y_new * y_new).sum(axis=0))
@@ -94,7 +102,7 @@ class RK45:
         p = self.p
         if eps == 0.0:
             return 5.0
-        return min(5.0, max(0.2, p.headroom * (p.max_err / eps) ** 0.2))
+        return min(5.0, max(0.2, p.headroom * (p.max_err / eps) ** self.EXPONENT))
 
     def adaptive_step(self, h_limit=None):
         """Attempts until one is accepted; returns the accepted step size."""
