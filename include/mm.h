@@ -122,8 +122,16 @@ int mm_set_solver(mm_ctx* ctx, double max_err, double headroom, double dt0,
  * stepping.  The array is copied. */
 int mm_set_fixed_dt_sequence(mm_ctx* ctx, const double* dts, int n);
 
-/* Takes n accepted RK45 steps (the paper's steps(n)).  In replay mode takes
- * min(n, remaining) steps. */
+/* Integrator (Sec. IV "Dynamics"): MM_RK45, Dormand-Prince 5(4), 6 new
+ * torque evaluations per attempt (default); MM_RK23, Bogacki-Shampine 3(2),
+ * 3 per attempt, step factor exponent 1/3.  Both reuse the last stage as the
+ * next first stage.  Switching keeps m, t, dt and the controller settings. */
+enum { MM_RK45 = 0, MM_RK23 = 1 };
+int mm_set_integrator(mm_ctx* ctx, int method);
+int mm_get_integrator(mm_ctx* ctx, int* method);
+
+/* Takes n accepted steps of the current integrator (the paper's steps(n)).
+ * In replay mode takes min(n, remaining) steps. */
 int mm_step(mm_ctx* ctx, int n);
 /* Advances to t_end exactly (the paper's run(t)); the last step is shortened
  * to land on t_end.  Returns MM_OK immediately if t >= t_end. */
@@ -141,6 +149,19 @@ int mm_get_torque(mm_ctx* ctx, float* tau);
 /* Energies from the effective field with float64 accumulation (Sec. III:
  * -1/2 M.B_demag, -1/2 M.B_exch, -1/2 B(Ku1).M - 1/4 B(Ku2).M, -M.B_ext). */
 int mm_get_energies(mm_ctx* ctx, mm_energies* e);
+/* Maximum over the magnetic cells of |dm/dt| (rad/s) at the current m and t,
+ * with the current precession switch (float32 torque, exact max). */
+int mm_get_max_torque(mm_ctx* ctx, double* tau_max);
+/* The paper's relax() (Sec. IV "Energy minimization"): with the precession
+ * term off and the RK23 solver, advances in blocks of 3 accepted steps while
+ * the total energy decreases, then while the maximum torque decreases; each
+ * time the torque stops decreasing MaxErr is divided by sqrt(2), and the
+ * level on which MaxErr first reaches 1e-9 is the last.  t advances as in a
+ * run.  Afterwards the integrator, MaxErr and the precession switch are those
+ * of before the call.  *steps_taken (may be NULL) receives the accepted steps.
+ * MM_ERR_TIMEOUT if a further block would exceed max_steps (the state reached
+ * so far is kept); MM_ERR_STATE in replay or surrogate mode or before set_m. */
+int mm_relax(mm_ctx* ctx, long long max_steps, long long* steps_taken);
 int mm_get_stats(mm_ctx* ctx, mm_stats* s);
 /* Sizes of the accepted steps since creation (up to `max` of them, oldest
  * first; the library keeps the first 1<<20); *n receives the count copied. */

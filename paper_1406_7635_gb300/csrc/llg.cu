@@ -51,8 +51,8 @@ __global__ void k_torque(Geom g, Buffers b, Terms T, Ptrs p, const DevState* __r
   const float* __restrict__ m = s == 0 ? (par ? p.m1 : p.m0) : b.ms;
   float* __restrict__ k = pick_k(p, k_role(s, par));
   const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
-  const int r = b.region[i];
-  if (!(b.mask[i] && b.lut->msat[r] > 0.0f)) {
+  const int r = b.code[i];
+  if (r == kVacuum) {
     k[i] = k[g.n + i] = k[2 * g.n + i] = 0.0f;
     return;
   }
@@ -135,15 +135,18 @@ __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict_
 
 // Getters: mode 0 writes B_eff, mode 1 the torque, mode 2 accumulates energies
 // (float64) into acc[0..7] = {demag, exch, anis, zeeman, mx, my, mz, ncells}
-// (M.B sums; the host multiplies by the cell volume).
+// (M.B sums; the host multiplies by the cell volume), mode 4 the maximum of
+// |torque| over the magnetic cells into the first 4 bytes of acc (float bits,
+// atomicMax; the host zeroes them first).
 __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict__ m, const DevState* __restrict__ st,
                             int mode, double freq, double phase_over_pi) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float tmax = 0.0f;
   if (i < g.n) {
     const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
-    const int r = b.region[i];
-    const bool mag = b.mask[i] && b.lut->msat[r] > 0.0f;
+    const int r = b.code[i];
+    const bool mag = r != kVacuum;
     float3 out = f3(0, 0, 0);
     if (mag) {
       const float3 mi = f3(m[i], m[g.n + i], m[2 * g.n + i]);
@@ -153,7 +156,11 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
       const float3 B = total(P);
       if (mode == 0) out = B;
       else if (mode == 1) out = llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession);
-      else {
+      else if (mode == 4) {
+        const float3 tq = llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession);
+        tmax = sqrtf(tq.x * tq.x + tq.y * tq.y + tq.z * tq.z);
+        if (!(tmax <= FLT_MAX)) tmax = __int_as_float(0x7f800000);
+      } else {
         const double ms = b.lut->msat[r];
         auto dot = [&](float3 v) { return ms * ((double)mi.x * v.x + (double)mi.y * v.y + (double)mi.z * v.z); };
         acc[0] = -0.5 * dot(P.demag);
@@ -171,6 +178,10 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
       b.out[g.n + i] = out.y;
       b.out[2 * g.n + i] = out.z;
     }
+  }
+  if (mode == 4) {
+    for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(b.acc), __float_as_uint(tmax));
   }
   if (mode == 2) {
     __shared__ double red[8][32];
@@ -199,6 +210,13 @@ __global__ void k_normalize(Geom g, const uint8_t* __restrict__ mask, const uint
   m[i] = x * inv;
   m[g.n + i] = y * inv;
   m[2 * g.n + i] = z * inv;
+}
+
+__global__ void k_codes(Geom g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ region,
+                        const RegionLUT* __restrict__ lut, int* __restrict__ code) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  code[i] = is_magnetic(mask, region, lut, i) ? (int)region[i] : kVacuum;
 }
 
 __global__ void k_copy_cur(Geom g, const float* __restrict__ m0, const float* __restrict__ m1,
@@ -249,6 +267,10 @@ void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const f
 
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s) {
   k_normalize<<<blocks(g.n), kT, 0, s>>>(g, b.mask, b.region, b.lut, m);
+}
+
+void launch_codes(const Geom& g, const Buffers& b, cudaStream_t s) {
+  k_codes<<<blocks(g.n), kT, 0, s>>>(g, b.mask, b.region, b.lut, b.code);
 }
 
 void launch_copy_mcur(const Geom& g, const Buffers& b, float* dst, cudaStream_t s) {

@@ -23,6 +23,17 @@ __constant__ double kA[7][6] = {
 __constant__ double kE[7] = {71.0 / 57600.0,      0.0,           -71.0 / 16695.0, 71.0 / 1920.0,
                              -17253.0 / 339200.0, 22.0 / 525.0, -1.0 / 40.0};
 
+// Bogacki & Shampine (1989) 3(2) pair, the solver of relax() (Sec. IV).  Its
+// four stages occupy the RK45 stage slots 0, 1, 2 and 6, so the last stage
+// takes part in the same FSAL buffer swap (slot 6 <-> slot 0) and the stage
+// kernels serve both methods unchanged: row = slot of the stage, column =
+// slot of the earlier stage it reads.
+__device__ __forceinline__ int slot23(int s) { return s == 3 ? 6 : s; }
+__constant__ double kC23[4] = {0.0, 0.5, 0.75, 1.0};
+__constant__ double kA23[4][3] = {{0, 0, 0}, {0.5, 0, 0}, {0.0, 0.75, 0}, {2.0 / 9.0, 1.0 / 3.0, 4.0 / 9.0}};
+// 3rd-order weights (2/9, 1/3, 4/9, 0) minus 2nd-order weights (7/24, 1/4, 1/3, 1/8)
+__constant__ double kE23[4] = {-5.0 / 72.0, 1.0 / 12.0, 1.0 / 9.0, -1.0 / 8.0};
+
 // stage coefficients of the current attempt, h * a_sj and h * e_j, in float
 struct StageCoef {
   float ah[7][6];
@@ -69,29 +80,9 @@ struct FieldParts {
 
 __device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
 
-__device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const Terms& T, const float* __restrict__ m, long long i,
-                         int x, int y, int z, int r, float3 mi, float sinft, float3 bdemag, FieldParts& P) {
-  const RegionLUT* __restrict__ lut = b.lut;
-  P.demag = T.demag ? bdemag : f3(0, 0, 0);
-  float3 ex = f3(0, 0, 0);
-  if (T.exch) {
-    const float* __restrict__ xl = b.xlut + r * kRegions;
-    auto nb = [&](long long j, float id2) {
-      if (!is_magnetic(b.mask, b.region, lut, j)) return;
-      const float c = __ldg(&xl[b.region[j]]) * id2;
-      ex.x += c * (m[j] - mi.x);
-      ex.y += c * (m[g.n + j] - mi.y);
-      ex.z += c * (m[2 * g.n + j] - mi.z);
-    };
-    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
-    if (x > 0) nb(i - sx, g.idx2);
-    if (x < g.nx - 1) nb(i + sx, g.idx2);
-    if (y > 0) nb(i - sy, g.idy2);
-    if (y < g.ny - 1) nb(i + sy, g.idy2);
-    if (z > 0) nb(i - sz, g.idz2);
-    if (z < g.nz - 1) nb(i + sz, g.idz2);
-  }
-  P.exch = ex;
+// uniaxial anisotropy (Ku1 and Ku2 parts) and Zeeman field of region r
+__device__ __forceinline__ void field_local(const RegionLUT* __restrict__ lut, const Terms& T, int r, float3 mi,
+                                            float sinft, FieldParts& P) {
   if (T.anis) {
     const float ux = __ldg(&lut->u[0][r]), uy = __ldg(&lut->u[1][r]), uz = __ldg(&lut->u[2][r]);
     const float um = ux * mi.x + uy * mi.y + uz * mi.z;
@@ -109,6 +100,37 @@ __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const 
   } else {
     P.zee = f3(0, 0, 0);
   }
+}
+
+// Effective field at cell i of code ci (a magnetic cell: ci < kVacuum).
+// Exchange: the six neighbours are read unconditionally; a neighbour outside
+// the grid is replaced by the cell itself (m_j - m_i = 0) and a vacuum
+// neighbour has a zero coupling, so the loads carry no branches.
+__device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const Terms& T, const float* __restrict__ m,
+                                         long long i, int x, int y, int z, int ci, float3 mi, float sinft,
+                                         float3 bdemag, FieldParts& P) {
+  const RegionLUT* __restrict__ lut = b.lut;
+  const int r = ci & (kRegions - 1);
+  P.demag = T.demag ? bdemag : f3(0, 0, 0);
+  float3 ex = f3(0, 0, 0);
+  if (T.exch) {
+    const float* __restrict__ xl = b.xlut + r * kXStride;
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const long long js[6] = {x > 0 ? i - 1 : i,          x < g.nx - 1 ? i + 1 : i,
+                             y > 0 ? i - sy : i,         y < g.ny - 1 ? i + sy : i,
+                             z > 0 ? i - sz : i,         z < g.nz - 1 ? i + sz : i};
+    const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const long long j = js[d];
+      const float c = __ldg(&xl[b.code[j]]) * id2[d];
+      ex.x += c * (m[j] - mi.x);
+      ex.y += c * (m[g.n + j] - mi.y);
+      ex.z += c * (m[2 * g.n + j] - mi.z);
+    }
+  }
+  P.exch = ex;
+  field_local(lut, T, r, mi, sinft, P);
 }
 
 __device__ __forceinline__ float3 total(const FieldParts& P) {
@@ -140,6 +162,20 @@ __device__ void prepare_attempt(DevState* st, StageCoef* sc, const double* __res
   else if (st->mode == 1) h = fmin(st->dt, st->t_end - st->t);
   else h = st->dt;
   st->h = h;
+  if (st->method == 1) {
+    for (int s = 0; s < 7; ++s) {
+      st->stage_t[s] = st->t;
+      for (int j = 0; j < 6; ++j) sc->ah[s][j] = 0.0f;
+      sc->eh[s] = 0.0f;
+    }
+    for (int s = 0; s < 4; ++s) {
+      const int r = slot23(s);
+      st->stage_t[r] = st->t + kC23[s] * h;
+      for (int j = 0; j < s; ++j) sc->ah[r][slot23(j)] = (float)(kA23[s][j] * h);
+      sc->eh[r] = (float)(kE23[s] * h);
+    }
+    return;
+  }
   for (int s = 0; s < 7; ++s) {
     st->stage_t[s] = st->t + kC[s] * h;
     for (int j = 0; j < 6; ++j) sc->ah[s][j] = (float)(kA[s][j] * h);
@@ -155,7 +191,8 @@ __device__ void check_done(DevState* st) {
 
 // The controller (Sec. IV, "Adaptive time step"): eps = max |tau_5 - tau_4| dt
 // against MaxErr with headroom 0.8.  Readings: accept iff eps <= MaxErr;
-// dt_new = dt clamp(0.8 (MaxErr/eps)^(1/5), 0.2, 5), bounded by dt_max, and
+// dt_new = dt clamp(0.8 (MaxErr/eps)^(1/5), 0.2, 5) (exponent 1/3 for RK23,
+// whose error estimate is of order 2), bounded by dt_max, and
 // at least dt_min after an accepted step; a rejection that would need a step
 // below dt_min ends the call with MM_ERR_DT_UNDERFLOW.
 __device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ hist,
@@ -163,7 +200,7 @@ __device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ his
   const double eps = (double)__uint_as_float(st->err_bits);
   st->err_bits = 0;
   st->ticket = 0;
-  st->evals += 6;
+  st->evals += st->method == 1 ? 3 : 6;
   st->call_attempts++;
   st->last_err = eps;
   if (!(eps <= DBL_MAX)) {
@@ -174,7 +211,8 @@ __device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ his
   const double h = st->h;
   const bool replay = st->mode == 2;
   const bool accept = replay || eps <= st->max_err;
-  const double factor = eps == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, st->headroom * pow(st->max_err / eps, 0.2)));
+  const double ex = st->method == 1 ? 1.0 / 3.0 : 0.2;
+  const double factor = eps == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, st->headroom * pow(st->max_err / eps, ex)));
   const double ndt = fmin(h * factor, st->dt_max);
   if (accept) {
     st->t += h;

@@ -66,7 +66,7 @@ struct mm_ctx {
   double b0[kRegions][3]{}, b1[kRegions][3]{};
   double freq = 0, phase = 0;
   Terms T{1, 1, 1, 1};
-  int precession = 1;
+  int method = 0;                // host copy of DevState::method
   bool lut_dirty = true;
   bool m_set = false;
   bool k1_valid = false;
@@ -107,7 +107,7 @@ int write_state(mm_ctx* c) {
 int flush_luts(mm_ctx* c) {
   if (!c->lut_dirty) return MM_OK;
   RegionLUT L{};
-  std::vector<float> X((size_t)kRegions * kRegions, 0.0f);
+  std::vector<float> X((size_t)kRegions * kXStride, 0.0f);
   double a[kRegions];
   for (int r = 0; r < kRegions; ++r) {
     const mm_material& m = c->mat[r];
@@ -130,10 +130,12 @@ int flush_luts(mm_ctx* c) {
     for (int r2 = 0; r2 < kRegions; ++r2) {
       const double s = a[r1] + a[r2];
       const double h = s != 0.0 ? 2.0 * a[r1] * a[r2] / s : 0.0;
-      X[(size_t)r1 * kRegions + r2] = (float)(2.0 * c->S[(size_t)r1 * kRegions + r2] * h);
+      X[(size_t)r1 * kXStride + r2] = (float)(2.0 * c->S[(size_t)r1 * kRegions + r2] * h);
     }
   MM_CUDA(cudaMemcpyAsync(c->b.lut, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
   MM_CUDA(cudaMemcpyAsync(c->b.xlut, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  launch_codes(c->g, c->b, c->stream);
+  MM_CUDA(cudaGetLastError());
   MM_CUDA(cudaStreamSynchronize(c->stream));
   c->lut_dirty = false;
   return MM_OK;
@@ -161,7 +163,7 @@ void enqueue_demag(mm_ctx* c) {
 
 // The row-stage path (fused convolution layout, exact demag): per attempt one
 // prep kernel, then per stage the (y, z) transform and one row kernel.
-bool rowstage_path(const mm_ctx* c) { return c->g.fused && !c->sur_active; }
+bool rowstage_path(const mm_ctx* c) { return c->g.fused && !c->sur_active && c->method == 0; }
 
 // stage-1 torque at the current m (FSAL start)
 void enqueue_k1(mm_ctx* c) {
@@ -187,10 +189,15 @@ void enqueue_attempt(mm_ctx* c) {
     }
     return;
   }
-  for (int s = 1; s < 7; ++s) {
-    launch_stage_input(c->g, c->b, s, c->stream);
+  // stage slots of the attempt: RK45 uses 1..6; RK23 its stages 2..4 in
+  // slots 1, 2 and 6 (the slot of the FSAL stage)
+  static const int kRK45[6] = {1, 2, 3, 4, 5, 6}, kRK23[3] = {1, 2, 6};
+  const int* slots = c->method == 1 ? kRK23 : kRK45;
+  const int ns = c->method == 1 ? 3 : 6;
+  for (int i = 0; i < ns; ++i) {
+    launch_stage_input(c->g, c->b, slots[i], c->stream);
     enqueue_demag(c);
-    launch_torque_t(c->g, c->b, c->T, s, c->freq, c->phase, c->stream);
+    launch_torque_t(c->g, c->b, c->T, slots[i], c->freq, c->phase, c->stream);
   }
   launch_error_control(c->g, c->b, c->stream);
 }
@@ -268,7 +275,7 @@ int eval_field(mm_ctx* c, int mode) {
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
   if (c->T.demag || mode == 3) launch_demag(c->g, nb, c->b.ms, c->stream);
   if (mode == 3) return MM_OK;
-  if (mode == 2) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 8 * sizeof(double), c->stream));
+  if (mode == 2 || mode == 4) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 8 * sizeof(double), c->stream));
   Terms T = c->T;
   launch_field_out_t(c->g, c->b, T, c->b.ms, mode, c->freq, c->phase, c->stream);
   MM_CUDA(cudaGetLastError());
@@ -365,7 +372,8 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   alloc((void**)&b.mask, (size_t)g.n);
   alloc((void**)&b.region, (size_t)g.n);
   alloc((void**)&b.lut, sizeof(RegionLUT));
-  alloc((void**)&b.xlut, (size_t)kRegions * kRegions * sizeof(float));
+  alloc((void**)&b.xlut, (size_t)kRegions * kXStride * sizeof(float));
+  alloc((void**)&b.code, (size_t)g.n * sizeof(int));
   alloc((void**)&b.st, devstate_bytes());
   alloc((void**)&b.hist, (size_t)kHistCap * sizeof(double));
   alloc((void**)&b.acc, 8 * sizeof(double));
@@ -412,6 +420,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   launch_demag(g, nb, b.ms, c->stream);
   e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && g.fused) e = prepare_rowstage(g);
   if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, std::string("warm-up: ") + cudaGetErrorString(e)));
   *out = c;
   return MM_OK;
@@ -424,8 +433,8 @@ int mm_destroy(mm_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   Buffers& b = c->b;
   void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.ms2, b.bd, b.out,
-                  b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.st, b.hist, b.acc, b.fixed,
-                  c->sur_acc};
+                  b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.code, b.st, b.hist, b.acc,
+                  b.fixed, c->sur_acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -441,6 +450,7 @@ int mm_set_geometry(mm_ctx* c, const uint8_t* mask) {
     for (long long i = 0; i < c->g.n; ++i) v[i] = mask[i] ? 1 : 0;
   MM_CUDA(cudaMemcpyAsync(c->b.mask, v.data(), v.size(), cudaMemcpyHostToDevice, c->stream));
   MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->lut_dirty = true;   // cell codes
   invalidate(c);
   return MM_OK;
 }
@@ -451,6 +461,7 @@ int mm_set_regions(mm_ctx* c, const uint8_t* region) {
   if (region) std::memcpy(v.data(), region, v.size());
   MM_CUDA(cudaMemcpyAsync(c->b.region, v.data(), v.size(), cudaMemcpyHostToDevice, c->stream));
   MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->lut_dirty = true;   // cell codes
   invalidate(c);
   return MM_OK;
 }
@@ -709,6 +720,142 @@ int mm_get_energies(mm_ctx* c, mm_energies* out) {
   return MM_OK;
 }
 
+int mm_get_max_torque(mm_ctx* c, double* tau_max) {
+  if (!c || !tau_max) return fail(MM_ERR_ARG, "NULL argument");
+  int rc = eval_field(c, 4);
+  if (rc) return rc;
+  unsigned int bits = 0;
+  MM_CUDA(cudaMemcpyAsync(&bits, c->b.acc, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  float v;
+  std::memcpy(&v, &bits, sizeof(v));
+  *tau_max = (double)v;
+  return MM_OK;
+}
+
+int mm_set_integrator(mm_ctx* c, int method) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (method != MM_RK45 && method != MM_RK23) return fail(MM_ERR_ARG, "method must be MM_RK45 or MM_RK23");
+  if (method == c->method) return MM_OK;
+  int rc = read_state(c);
+  if (rc) return rc;
+  c->st_host->method = method;
+  rc = write_state(c);
+  if (rc) return rc;
+  c->method = method;
+  c->graph_valid = false;     // the cached first stage (torque at m) stays valid
+  return MM_OK;
+}
+
+int mm_get_integrator(mm_ctx* c, int* method) {
+  if (!c || !method) return fail(MM_ERR_ARG, "NULL argument");
+  *method = c->method;
+  return MM_OK;
+}
+
+// relax() (Sec. IV, "Energy minimization"): precession off, RK23; advance in
+// blocks of kRelaxBlock accepted steps while the total energy decreases, then
+// while the maximum torque decreases, lowering MaxErr by sqrt(2) each time it
+// stops, until MaxErr <= 1e-9.  The solver, MaxErr and the precession switch
+// are restored on every exit.
+namespace {
+constexpr int kRelaxBlock = 3;
+constexpr double kRelaxMinErr = 1e-9;
+
+int set_precession(mm_ctx* c, int on) {
+  int rc = read_state(c);
+  if (rc) return rc;
+  if (c->st_host->precession == on) return MM_OK;
+  c->st_host->precession = on;
+  rc = write_state(c);
+  if (rc) return rc;
+  c->graph_valid = false;
+  invalidate(c);              // the cached first-stage torque depends on it
+  return MM_OK;
+}
+
+int set_max_err(mm_ctx* c, double e) {
+  int rc = read_state(c);
+  if (rc) return rc;
+  c->st_host->max_err = e;
+  return write_state(c);
+}
+
+int relax_body(mm_ctx* c, long long max_steps, long long* taken) {
+  int rc = read_state(c);
+  if (rc) return rc;
+  const long long a0 = c->st_host->accepted;
+  double max_err = c->st_host->max_err;
+  auto steps_done = [&]() { return c->st_host->accepted - a0; };
+  auto block = [&]() -> int {
+    if (steps_done() + kRelaxBlock > max_steps) return fail(MM_ERR_TIMEOUT, "relax: step limit reached");
+    int r = drive(c, 0, kRelaxBlock, 0.0);
+    if (r) return r;
+    *taken = steps_done();
+    return MM_OK;
+  };
+  mm_energies e;
+  rc = mm_get_energies(c, &e);
+  if (rc) return rc;
+  double e0 = e.total;
+  for (;;) {
+    rc = block();
+    if (rc) return rc;
+    rc = mm_get_energies(c, &e);
+    if (rc) return rc;
+    if (!(e.total < e0)) break;
+    e0 = e.total;
+  }
+  double t0;
+  rc = mm_get_max_torque(c, &t0);
+  if (rc) return rc;
+  for (;;) {
+    rc = block();
+    if (rc) return rc;
+    double t1;
+    rc = mm_get_max_torque(c, &t1);
+    if (rc) return rc;
+    if (t1 < t0) {
+      t0 = t1;
+      continue;
+    }
+    if (max_err <= kRelaxMinErr) break;
+    max_err /= std::sqrt(2.0);
+    rc = set_max_err(c, max_err);
+    if (rc) return rc;
+    t0 = t1;
+  }
+  return MM_OK;
+}
+}  // namespace
+
+int mm_relax(mm_ctx* c, long long max_steps, long long* steps_taken) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (max_steps <= 0) return fail(MM_ERR_ARG, "max_steps must be > 0");
+  if (!c->m_set) return fail(MM_ERR_STATE, "m has not been set");
+  if (c->fixed_n > 0) return fail(MM_ERR_STATE, "relax() is not available in replay mode");
+  if (c->sur_active) return fail(MM_ERR_STATE, "relax() is not available with the demag surrogate");
+  int rc = read_state(c);
+  if (rc) return rc;
+  const int saved_prec = c->st_host->precession, saved_method = c->method;
+  const double saved_err = c->st_host->max_err;
+  long long taken = 0;
+  rc = set_precession(c, 0);
+  if (!rc) rc = mm_set_integrator(c, MM_RK23);
+  if (!rc) rc = relax_body(c, max_steps, &taken);
+  const std::string msg = rc ? g_err : std::string();
+  // restore (errors here take precedence only if the relaxation succeeded)
+  int r2 = set_max_err(c, saved_err);
+  if (!r2) r2 = set_precession(c, saved_prec);
+  if (!r2) r2 = mm_set_integrator(c, saved_method);
+  if (steps_taken) *steps_taken = taken;
+  if (rc) {
+    g_err = msg;
+    return rc;
+  }
+  return r2;
+}
+
 int mm_get_stats(mm_ctx* c, mm_stats* s) {
   if (!c || !s) return fail(MM_ERR_ARG, "NULL argument");
   int rc = read_state(c);
@@ -794,6 +941,10 @@ int mm_set_state(mm_ctx* c, const void* buf, size_t bytes) {
   MM_CUDA(cudaStreamSynchronize(c->stream));
   c->m_set = true;
   c->k1_valid = h.k1_valid != 0;
+  if (c->method != s.method) {
+    c->method = s.method;
+    c->graph_valid = false;
+  }
   return MM_OK;
 }
 

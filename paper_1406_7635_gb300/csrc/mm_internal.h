@@ -8,6 +8,11 @@
 namespace mm {
 
 constexpr int kRegions = 256;
+// cell code: the region index of a cell that carries a magnetisation (mask
+// set, Msat > 0), kVacuum otherwise; the exchange table has a zero column at
+// kVacuum, so a vacuum neighbour contributes nothing without a branch
+constexpr int kVacuum = kRegions;
+constexpr int kXStride = kRegions + 1;   // row length of the exchange table
 constexpr int kHistCap = 1 << 20;   // accepted-step sizes kept for replay
 
 // Per-region parameters, float32, derived on the host from mm_material
@@ -60,6 +65,7 @@ struct DevState {
   unsigned int ticket;      // last-block election in the error kernel
   int call_attempts;         // attempts since the last begin
   int precession;
+  int method;               // 0 Dormand-Prince RK45, 1 Bogacki-Shampine RK23
 };
 
 struct Buffers {
@@ -75,7 +81,8 @@ struct Buffers {
   uint8_t* mask;
   uint8_t* region;
   RegionLUT* lut;
-  float* xlut;        // [256][256]: 2 S H(Aex/Msat) exchange couplings
+  float* xlut;        // [256][257]: 2 S H(Aex/Msat) exchange couplings, column 256 = 0
+  int* code;          // per cell: region, or kVacuum
   DevState* st;
   double* hist;       // accepted step sizes
   double* fixed;      // replay sequence
@@ -147,6 +154,11 @@ void launch_copy_mcur(const Geom& g, const Buffers& b, float* dst, cudaStream_t 
 void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const float* m, int mode, double freq,
                         double phase, cudaStream_t s);
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s);
+// cell codes from mask, region and the Msat table
+void launch_codes(const Geom& g, const Buffers& b, cudaStream_t s);
+// sets the launch attributes (dynamic shared memory) of the row-stage
+// kernels this grid uses; call outside stream capture
+cudaError_t prepare_rowstage(const Geom& g);
 
 // FNO surrogate (fno.cu)
 }  // namespace mm

@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
       out[i] = a0;
       out[g.n + i] = a1;
       out[2 * g.n + i] = a2;
-      const float ms = is_magnetic(b.mask, b.region, b.lut, i) ? __ldg(&b.lut->msat[b.region[i]]) : 0.f;
+      const int ci = b.code[i];
+      const float ms = ci != kVacuum ? __ldg(&b.lut->msat[ci]) : 0.f;
       v[0] = ms * a0;
       v[1] = ms * a1;
       v[2] = ms * a2;
@@ -95,19 +96,78 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
 }
 
+// Shared-memory layout of the row kernel (dynamic): the demag rows of the
+// block (3 ROWS pencils of L + 1 complex, padded to 16 bytes), then the
+// stencil rows of the stage input [3][NR][L] and their cell codes [NR][L].
+// Local stencil rows: 0 .. ROWS+1 are y0-1 .. y0+ROWS of plane z, then ROWS
+// rows y0 .. of plane z-1, then ROWS rows of plane z+1.
+template <int L, int ROWS>
+struct RsSmem {
+  static constexpr int PST = L + 1;
+  static constexpr int NR = 3 * ROWS + 2;
+  static constexpr int SPEC = ((3 * ROWS * PST * 8) + 15) / 16 * 16;
+  static constexpr int STEN = 3 * NR * L * 4;
+  static constexpr int CODE = NR * L * 4;
+  static constexpr int BYTES = SPEC + STEN + CODE;
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// asynchronous copies of the block's stencil rows (stage input and codes);
+// rows outside the grid are not copied and never read
+template <int L, int ROWS, int NT>
+__device__ __forceinline__ void stage_stencil(const Geom& g, const float* __restrict__ ms, const int* __restrict__ code,
+                                              float* sten, int* scode, int y0, int z) {
+  constexpr int NR = RsSmem<L, ROWS>::NR;
+  const bool vec = (g.nx & 3) == 0;      // rows start on 16-byte boundaries
+  const int w = vec ? 4 : 1;
+  const int cpr = (g.nx + w - 1) / w;
+  const int total = NR * 4 * cpr;
+  for (int e = threadIdx.x; e < total; e += NT) {
+    const int ch = e % cpr, t = e / cpr, a = t & 3, lr = t >> 2;
+    int yy = y0 + lr - 1, zz = z;
+    if (lr >= ROWS + 2) {
+      const int q = lr - (ROWS + 2);
+      yy = y0 + (q % ROWS);
+      zz = q < ROWS ? z - 1 : z + 1;
+    }
+    if (yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
+    const long long row = ((long long)zz * g.ny + yy) * g.nx + (long long)ch * w;
+    const void* src = a < 3 ? (const void*)(ms + a * g.n + row) : (const void*)(code + row);
+    void* dst = a < 3 ? (void*)(sten + (a * NR + lr) * L + ch * w) : (void*)(scode + lr * L + ch * w);
+    if (vec) cp_async16(dst, src);
+    else cp_async4(dst, src);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 template <int L, int ROWS, int NT>
 __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Ptrs p, DevState* __restrict__ st,
                                                  StageCoef* __restrict__ sc, int s, int mode, double freq,
                                                  double phase_over_pi) {
   if (st->done) return;   // uniform: the controller runs after every block of this launch
-  constexpr int PST = L + 1;
+  using SM = RsSmem<L, ROWS>;
+  constexpr int PST = SM::PST, NR = SM::NR;
   // real cells per thread: ROWS rows of at most L cells (nx <= 2L, and the
   // x-padding cells are not visited)
   constexpr int CPT = (ROWS * L + NT - 1) / NT;
-  __shared__ float2 sm[3 * ROWS * PST];
+  extern __shared__ float4 rs_dyn[];
+  float2* sm = reinterpret_cast<float2*>(rs_dyn);
+  float* sten = reinterpret_cast<float*>(reinterpret_cast<char*>(rs_dyn) + SM::SPEC);
+  int* scode = reinterpret_cast<int*>(reinterpret_cast<char*>(rs_dyn) + SM::SPEC + SM::STEN);
   __shared__ float2 twl[L], tw2[L + 1];
   __shared__ float wmax[32];
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
+  const float* __restrict__ ms = stage_buf(b, s);
+  // 0. stencil rows of the stage input arrive while the x transform runs
+  stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
   load_tables<L, NT>(twl, tw2, b.tw);
   // 1. x C2R of the demag spectrum rows (3 components)
   for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
@@ -136,40 +196,105 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   }
   __syncthreads();
   FftG<L, 1, 3 * ROWS, NT, 1, PST, 1, L>::run(sm, twl);
-  // 2. field and torque of the block's cells
-  const float* sf = reinterpret_cast<const float*>(sm);
   const int par = st->parity;
-  const float* __restrict__ ms = stage_buf(b, s);
+  const float* __restrict__ m = par ? p.m1 : p.m0;
+  const int ncell = ROWS * g.nx;
+  // 2. sums over the earlier stages at the block's cells (global streams):
+  //    next stage m + dt sum_j a_{s+1,j} k_j, or the error sum dt sum_j e_j k_j
+  float av[CPT][3];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int e = threadIdx.x + q * NT;
+    av[q][0] = av[q][1] = av[q][2] = 0.f;
+    if (mode == ROW_K1 || e >= ncell) continue;
+    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
+    if (y >= g.ny) continue;
+    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    if (mode == ROW_NEXT) {
+      float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
+      for (int j = 0; j < s; ++j) {
+        const float a = sc->ah[s + 1][j];
+        if (a == 0.0f) continue;
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
+        a0 = fmaf(a, k[i], a0);
+        a1 = fmaf(a, k[g.n + i], a1);
+        a2 = fmaf(a, k[2 * g.n + i], a2);
+      }
+      av[q][0] = a0;
+      av[q][1] = a1;
+      av[q][2] = a2;
+    } else {
+      float ex = 0.f, ey = 0.f, ez = 0.f;
+      for (int j = 0; j < 6; ++j) {
+        const float c = sc->eh[j];
+        if (c == 0.0f) continue;
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
+        ex = fmaf(c, k[i], ex);
+        ey = fmaf(c, k[g.n + i], ey);
+        ez = fmaf(c, k[2 * g.n + i], ez);
+      }
+      av[q][0] = ex;
+      av[q][1] = ey;
+      av[q][2] = ez;
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  // 3. field and torque of the block's cells, stencil from shared memory
+  const float* sf = reinterpret_cast<const float*>(sm);
+  const RegionLUT* __restrict__ lut = b.lut;
   float* __restrict__ kout = pick_k(p, k_role(s, par));
   const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->stage_t[s]) : 0.0f;
-  // each thread's cells: e = tid + q NT over the ROWS x nx real cells
-  const int ncell = ROWS * g.nx;
-  float kv[CPT][3];
-  bool magv[CPT];
+  float kv[CPT][3], mv[CPT][3];
+  int cv[CPT];
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int e = threadIdx.x + q * NT;
     kv[q][0] = kv[q][1] = kv[q][2] = 0.f;
-    magv[q] = false;
+    mv[q][0] = mv[q][1] = mv[q][2] = 0.f;
+    cv[q] = kVacuum;
     if (e >= ncell) continue;
     const int x = e % g.nx, r = e / g.nx, y = y0 + r;
     if (y >= g.ny) continue;
-    const long long i = ((long long)z * g.ny + y) * g.nx + x;
-    const int reg = b.region[i];
-    if (b.mask[i] && b.lut->msat[reg] > 0.0f) {
-      magv[q] = true;
-      const float3 mi = f3(ms[i], ms[g.n + i], ms[2 * g.n + i]);
-      const float3 bdem = f3(sf[2 * (0 * ROWS + r) * PST + x], sf[2 * (1 * ROWS + r) * PST + x],
-                             sf[2 * (2 * ROWS + r) * PST + x]);
-      FieldParts P;
-      field_at(g, b, T, ms, i, x, y, z, reg, mi, sinft, bdem, P);
-      const float3 tq = llg_torque(mi, total(P), b.lut->gfac[reg], b.lut->alpha[reg], st->precession);
-      kv[q][0] = tq.x;
-      kv[q][1] = tq.y;
-      kv[q][2] = tq.z;
+    const int C = (r + 1) * L + x;
+    const int ci = scode[C];
+    cv[q] = ci;
+    const float3 mi = f3(sten[C], sten[NR * L + C], sten[2 * NR * L + C]);
+    mv[q][0] = mi.x;
+    mv[q][1] = mi.y;
+    mv[q][2] = mi.z;
+    if (ci == kVacuum) continue;
+    FieldParts P;
+    P.demag = T.demag ? f3(sf[2 * (0 * ROWS + r) * PST + x], sf[2 * (1 * ROWS + r) * PST + x],
+                           sf[2 * (2 * ROWS + r) * PST + x])
+                      : f3(0, 0, 0);
+    float3 ex = f3(0, 0, 0);
+    if (T.exch) {
+      // same neighbour order and arithmetic as field_at
+      const float* __restrict__ xl = b.xlut + ci * kXStride;
+      const int nb[6] = {x > 0 ? C - 1 : C,
+                         x < g.nx - 1 ? C + 1 : C,
+                         y > 0 ? C - L : C,
+                         y < g.ny - 1 ? C + L : C,
+                         z > 0 ? (ROWS + 2 + r) * L + x : C,
+                         z < g.nz - 1 ? (2 * ROWS + 2 + r) * L + x : C};
+      const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int j = nb[d];
+        const float c = __ldg(&xl[scode[j]]) * id2[d];
+        ex.x += c * (sten[j] - mi.x);
+        ex.y += c * (sten[NR * L + j] - mi.y);
+        ex.z += c * (sten[2 * NR * L + j] - mi.z);
+      }
     }
+    P.exch = ex;
+    field_local(lut, T, ci, mi, sinft, P);
+    const float3 tq = llg_torque(mi, total(P), __ldg(&lut->gfac[ci]), __ldg(&lut->alpha[ci]), st->precession);
+    kv[q][0] = tq.x;
+    kv[q][1] = tq.y;
+    kv[q][2] = tq.z;
   }
-  // stores after all loads of the block's cells were issued
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int e = threadIdx.x + q * NT;
@@ -182,9 +307,8 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     kout[2 * g.n + i] = kv[q][2];
   }
   if (mode == ROW_K1) return;
-  const float* __restrict__ m = par ? p.m1 : p.m0;
   if (mode == ROW_NEXT) {
-    // 3. next stage input and its x R2C
+    // 4. next stage input and its x R2C
     __syncthreads();   // every thread is done reading B_demag from sm
     float* sw = reinterpret_cast<float*>(sm);
     float* __restrict__ nxt = stage_buf(b, s + 1);
@@ -193,29 +317,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       const int x = e % (2 * L), row = e / (2 * L), r = row % ROWS;
       if (x >= g.nx || y0 + r >= g.ny) sw[2 * row * PST + x] = 0.f;
     }
-    float nv[CPT][3];
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      const int e = threadIdx.x + q * NT;
-      nv[q][0] = nv[q][1] = nv[q][2] = 0.f;
-      if (e >= ncell) continue;
-      const int x = e % g.nx, r = e / g.nx, y = y0 + r;
-      if (y >= g.ny) continue;
-      const long long i = ((long long)z * g.ny + y) * g.nx + x;
-      float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
-      for (int j = 0; j < s; ++j) {
-        const float a = sc->ah[s + 1][j];
-        if (a == 0.0f) continue;
-        const float* __restrict__ k = pick_k(p, k_role(j, par));
-        a0 = fmaf(a, k[i], a0);
-        a1 = fmaf(a, k[g.n + i], a1);
-        a2 = fmaf(a, k[2 * g.n + i], a2);
-      }
-      const float a = sc->ah[s + 1][s];
-      nv[q][0] = fmaf(a, kv[q][0], a0);
-      nv[q][1] = fmaf(a, kv[q][1], a1);
-      nv[q][2] = fmaf(a, kv[q][2], a2);
-    }
+    const float a = sc->ah[s + 1][s];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int e = threadIdx.x + q * NT;
@@ -223,19 +325,25 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       const int x = e % g.nx, r = e / g.nx, y = y0 + r;
       if (y >= g.ny) continue;
       const long long i = ((long long)z * g.ny + y) * g.nx + x;
-      nxt[i] = nv[q][0];
-      nxt[g.n + i] = nv[q][1];
-      nxt[2 * g.n + i] = nv[q][2];
-      const float msat = magv[q] ? __ldg(&b.lut->msat[b.region[i]]) : 0.f;
-      for (int c = 0; c < 3; ++c) sw[2 * (c * ROWS + r) * PST + x] = msat * nv[q][c];
+      const float n0 = fmaf(a, kv[q][0], av[q][0]);
+      const float n1 = fmaf(a, kv[q][1], av[q][1]);
+      const float n2 = fmaf(a, kv[q][2], av[q][2]);
+      nxt[i] = n0;
+      nxt[g.n + i] = n1;
+      nxt[2 * g.n + i] = n2;
+      const float msat = cv[q] != kVacuum ? __ldg(&lut->msat[cv[q]]) : 0.f;
+      sw[2 * (0 * ROWS + r) * PST + x] = msat * n0;
+      sw[2 * (1 * ROWS + r) * PST + x] = msat * n1;
+      sw[2 * (2 * ROWS + r) * PST + x] = msat * n2;
     }
     __syncthreads();
     rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
     return;
   }
-  // 3'. last stage: error estimate, candidate m, block max, controller
+  // 4'. last stage: error estimate, candidate m, block max, controller
   float emax = 0.f;
   float* __restrict__ mnew = par ? p.m0 : p.m1;
+  const float e6 = sc->eh[6];
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int e = threadIdx.x + q * NT;
@@ -243,20 +351,14 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     const int x = e % g.nx, r = e / g.nx, y = y0 + r;
     if (y >= g.ny) continue;
     const long long i = ((long long)z * g.ny + y) * g.nx + x;
-    if (magv[q]) {
-      float ex = sc->eh[6] * kv[q][0], ey = sc->eh[6] * kv[q][1], ez = sc->eh[6] * kv[q][2];
-      for (int j = 0; j < 6; ++j) {
-        const float c = sc->eh[j];
-        if (c == 0.0f) continue;
-        const float* __restrict__ k = pick_k(p, k_role(j, par));
-        ex = fmaf(c, k[i], ex);
-        ey = fmaf(c, k[g.n + i], ey);
-        ez = fmaf(c, k[2 * g.n + i], ez);
-      }
+    if (cv[q] != kVacuum) {
+      const float ex = fmaf(e6, kv[q][0], av[q][0]);
+      const float ey = fmaf(e6, kv[q][1], av[q][1]);
+      const float ez = fmaf(e6, kv[q][2], av[q][2]);
       float err = sqrtf(ex * ex + ey * ey + ez * ez);
       if (!(err <= FLT_MAX)) err = __int_as_float(0x7f800000);
       emax = fmaxf(emax, err);
-      const float mx = ms[i], my = ms[g.n + i], mz = ms[2 * g.n + i];
+      const float mx = mv[q][0], my = mv[q][1], mz = mv[q][2];
       const float inv = rsqrtf(mx * mx + my * my + mz * mz);
       mnew[i] = mx * inv;
       mnew[g.n + i] = my * inv;
@@ -307,21 +409,48 @@ void launch_rs(const Geom& g, const Buffers& b, const Terms& T, int kind, int s,
   if (kind == 0)
     k_rs_prep<L, ROWS, C::NT><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s);
   else
-    k_rs_row<L, ROWS, C::NT><<<grid, C::NT, 0, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq,
-                                                      phase / 3.14159265358979323846);
+    k_rs_row<L, ROWS, C::NT><<<grid, C::NT, RsSmem<L, ROWS>::BYTES, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode,
+                                                                          freq, phase / 3.14159265358979323846);
 }
+
+template <int L, int ROWS>
+cudaError_t prepare_rs() {
+  return cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              RsSmem<L, ROWS>::BYTES);
+}
+
+template <int L>
+struct RsRows {
+  static constexpr int R1 = L >= 1024 ? 1 : 1024 / L;
+  static constexpr int R2 = L >= 256 ? 1 : 256 / L;
+  static bool big(const Geom& g) { return (long long)((g.ny + R1 - 1) / R1) * g.nz >= 300; }
+};
 
 template <int L>
 void launch_rs_l(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
                  double phase, cudaStream_t st) {
-  constexpr int R1 = L >= 1024 ? 1 : 1024 / L;
-  constexpr int R2 = L >= 256 ? 1 : 256 / L;
-  const long long blocks1 = (long long)((g.ny + R1 - 1) / R1) * g.nz;
-  if (blocks1 >= 300) launch_rs<L, R1>(g, b, T, kind, s, mode, freq, phase, st);
-  else launch_rs<L, R2>(g, b, T, kind, s, mode, freq, phase, st);
+  if (RsRows<L>::big(g)) launch_rs<L, RsRows<L>::R1>(g, b, T, kind, s, mode, freq, phase, st);
+  else launch_rs<L, RsRows<L>::R2>(g, b, T, kind, s, mode, freq, phase, st);
+}
+
+template <int L>
+cudaError_t prepare_rs_l(const Geom& g) {
+  return RsRows<L>::big(g) ? prepare_rs<L, RsRows<L>::R1>() : prepare_rs<L, RsRows<L>::R2>();
 }
 
 }  // namespace
+
+cudaError_t prepare_rowstage(const Geom& g) {
+  switch (g.lx) {
+    case 16: return prepare_rs_l<16>(g);
+    case 32: return prepare_rs_l<32>(g);
+    case 64: return prepare_rs_l<64>(g);
+    case 128: return prepare_rs_l<128>(g);
+    case 256: return prepare_rs_l<256>(g);
+    case 512: return prepare_rs_l<512>(g);
+    default: return cudaSuccess;
+  }
+}
 
 // kind 0: prep of stage s; kind 1: row kernel of stage s with mode 0 (first
 // stage only), 1 (next stage), 2 (last stage: error and controller)

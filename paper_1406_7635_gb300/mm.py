@@ -20,6 +20,7 @@ if not os.path.exists(LIB):
 _lib = C.CDLL(LIB)
 
 MM_OK = 0
+MM_RK45, MM_RK23 = 0, 1
 ERRORS = {-1: "MM_ERR_ARG", -2: "MM_ERR_CUDA", -3: "MM_ERR_OOM", -4: "MM_ERR_NONFINITE",
           -5: "MM_ERR_DT_UNDERFLOW", -6: "MM_ERR_TIMEOUT", -7: "MM_ERR_STATE"}
 
@@ -85,6 +86,10 @@ _SIGS = {
     "mm_get_torque": (_I, [_P, _P]),
     "mm_get_energies": (_I, [_P, C.POINTER(mm_energies)]),
     "mm_get_stats": (_I, [_P, C.POINTER(mm_stats)]),
+    "mm_get_max_torque": (_I, [_P, C.POINTER(_D)]),
+    "mm_set_integrator": (_I, [_P, _I]),
+    "mm_get_integrator": (_I, [_P, C.POINTER(_I)]),
+    "mm_relax": (_I, [_P, C.c_longlong, C.POINTER(C.c_longlong)]),
     "mm_get_dt_history": (_I, [_P, _P, _I, C.POINTER(_I)]),
     "mm_state_bytes": (C.c_size_t, [_P]),
     "mm_get_state": (_I, [_P, _P, C.c_size_t]),
@@ -261,6 +266,25 @@ class Context:
         _check(mm_get_energies(self.h, C.byref(e)))
         return {"total": e.total, "demag": e.demag, "exch": e.exch, "anis": e.anis, "zeeman": e.zeeman,
                 "m_avg": list(e.m_avg)}
+
+    def get_max_torque(self):
+        v = C.c_double()
+        _check(mm_get_max_torque(self.h, C.byref(v)))
+        return v.value
+
+    def set_integrator(self, method):
+        _check(mm_set_integrator(self.h, {"rk45": MM_RK45, "rk23": MM_RK23}.get(method, method)))
+
+    def get_integrator(self):
+        v = C.c_int()
+        _check(mm_get_integrator(self.h, C.byref(v)))
+        return v.value
+
+    def relax(self, max_steps=1_000_000):
+        """The paper's relax(); returns the accepted steps it took."""
+        n = C.c_longlong()
+        _check(mm_relax(self.h, int(max_steps), C.byref(n)))
+        return n.value
 
     def get_stats(self):
         s = mm_stats()
