@@ -332,6 +332,7 @@ def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
     from paper_1406_7635_gb300.workloads import batch_instances, problem_from_instance
     specs, m0s = batch_instances(512)
     b = mm.Batch(specs, device=local_rank)
+    tiles = [b.class_info(c) for c in range(b.num_classes())]
     for i, m in enumerate(m0s):
         b.set_m(i, m)
     b.run(1e-15)                      # warm-up: builds and instantiates the graph
@@ -370,7 +371,8 @@ def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
             "cell_steps_per_s": cell_steps / wall, "accepted_steps_mean": float(np.mean([s["accepted"] for s in stats])),
             "sequential_instances_per_s": len(specs) / seq_time,
             "speedup_vs_sequential": seq_time / wall,
-            "sequential_sample": f"{seq_per_shape} instances per grid size, same t_end, extrapolated by count"}
+            "sequential_sample": f"{seq_per_shape} instances per grid size, same t_end, extrapolated by count",
+            "autotuned_tiles": tiles}
 
 
 def run_surrogate(args, local_rank, steps=40):

@@ -300,6 +300,13 @@ int mm_batch_get_stats(mm_batch* b, int i, mm_stats* s);
 int mm_batch_get_dt_history(mm_batch* b, int i, double* dts, int max, int* n);
 /* Number of shape classes (distinct grids) in the batch. */
 int mm_batch_num_classes(mm_batch* b);
+/* FFT tiles of class c, picked at creation by timing every candidate of the
+ * class's convolution (no counterpart in the paper): info = {nx, ny, nz,
+ * instances, cly, clz, xrows} (residue split of the (y, z) transform across a
+ * cluster of cly*clz blocks; rows per block of the x-row kernels), *conv_us
+ * (may be NULL) = the chosen convolution's time for all the class's
+ * instances in microseconds. */
+int mm_batch_class_info(mm_batch* b, int c, int info[7], double* conv_us);
 
 #ifdef __cplusplus
 }

@@ -285,6 +285,7 @@ struct BClass {
   float* msat = nullptr;
   InstParams* prm = nullptr;
   double* hist = nullptr;
+  float conv_us = 0.f;      // autotuned convolution time of the whole class
 };
 
 }  // namespace mm
@@ -386,6 +387,49 @@ int build_batch_graph(mm_batch* B) {
   e = cudaGraphInstantiate(&B->exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return bfail(MM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  return MM_OK;
+}
+
+// FFT tile autotuner: for one class, time the convolution of all its
+// instances for every residue split and x-row block size the fused plan
+// allows (2 warm-up + 3 timed launches each, on the class's own buffers)
+// and keep the fastest.  Runs before any instance is marked done.
+int tune_class(mm_batch* B, BClass& C) {
+  int sp[4][2];
+  const int nsp = fused_splits(C.g, sp, 4);
+  int xr[3];
+  const int nxr = fused_xrows(C.g, xr, 3);
+  cudaEvent_t a = nullptr, z = nullptr;
+  MMB_CUDA(cudaEventCreate(&a));
+  MMB_CUDA(cudaEventCreate(&z));
+  Buffers bb = C.b;
+  bb.st = nullptr;
+  float best = 1e30f;
+  Geom bestg = C.g;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < nsp && e == cudaSuccess; ++i)
+    for (int j = 0; j < nxr && e == cudaSuccess; ++j) {
+      Geom g = C.g;
+      fused_set_split(g, sp[i][0], sp[i][1]);
+      g.xrows = xr[j];
+      for (int w = 0; w < 2; ++w) launch_demag_fused_batch(g, bb, C.b.ms, B->stream, bargs(B, C));
+      e = cudaEventRecord(a, B->stream);
+      for (int r = 0; r < 3; ++r) launch_demag_fused_batch(g, bb, C.b.ms, B->stream, bargs(B, C));
+      if (e == cudaSuccess) e = cudaEventRecord(z, B->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(z);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
+      if (e == cudaSuccess && ms / 3 < best) {
+        best = ms / 3;
+        bestg = g;
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(z);
+  if (e != cudaSuccess) return bfail(MM_ERR_CUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
+  C.g = bestg;
+  C.conv_us = best * 1e3f;
   return MM_OK;
 }
 
@@ -519,6 +563,11 @@ int mm_batch_create(mm_batch** out, int n, const mm_instance_spec* specs, int de
   }
   if (e != cudaSuccess)
     return cleanup(bfail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, cudaGetErrorString(e)));
+  // FFT tiles per class (instances are not yet marked done, buffers are zero)
+  for (int c = 0; c < nc; ++c) {
+    const int rc = tune_class(B, B->cls[c]);
+    if (rc) return cleanup(rc);
+  }
   // instance defaults (Sec. IV: MaxErr 1e-5, headroom 0.8); m along +x
   B->host_st.assign(n, InstState{});
   for (auto& s : B->host_st) {
@@ -682,5 +731,19 @@ int mm_batch_get_dt_history(mm_batch* B, int i, double* dts, int max, int* n) {
 }
 
 int mm_batch_num_classes(mm_batch* B) { return B ? (int)B->cls.size() : 0; }
+
+int mm_batch_class_info(mm_batch* B, int c, int info[7], double* conv_us) {
+  if (!B || !info || c < 0 || c >= (int)B->cls.size()) return bfail(MM_ERR_ARG, "bad batch or class index");
+  const BClass& C = B->cls[c];
+  info[0] = C.g.nx;
+  info[1] = C.g.ny;
+  info[2] = C.g.nz;
+  info[3] = C.B;
+  info[4] = C.g.cly;
+  info[5] = C.g.clz;
+  info[6] = C.g.xrows;
+  if (conv_us) *conv_us = C.conv_us;
+  return MM_OK;
+}
 
 }  // extern "C"

@@ -139,16 +139,19 @@ __host__ __device__ constexpr int ns_of(int L, int p) {
 // the global 2048-entry table, or a per-length copy in shared memory.
 // pre (first pass only, may be null): input element i is multiplied by pre[i]
 // as it is loaded.
-template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL>
+// WARP: the pencils belong to one warp (NT = 32, lanes share the butterflies,
+// __syncwarp() orders reads before writes) instead of the whole block.
+template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, bool WARP = false>
 __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw,
                                               const float2* __restrict__ pre = nullptr) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
   constexpr int PER = (TOT + NT - 1) / NT;
+  const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   float2 v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int b = threadIdx.x + q * NT;
+    const int b = tid + q * NT;
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
       const int base = (p / INNER) * BS + (p % INNER);
@@ -160,10 +163,11 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
       }
     }
   }
-  __syncthreads();
+  if (WARP) __syncwarp();
+  else __syncthreads();
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int b = threadIdx.x + q * NT;
+    const int b = tid + q * NT;
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
       const int base = (p / INNER) * BS + (p % INNER);
@@ -183,7 +187,8 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
       for (int r = 0; r < R; ++r) s[base + (o + r * NS) * ES] = v[q][r];
     }
   }
-  __syncthreads();
+  if (WARP) __syncwarp();
+  else __syncthreads();
 }
 
 // Full length-L complex transform of NP shared-memory pencils (in place,
@@ -202,6 +207,25 @@ struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, false> {
 };
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, true> {
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr) {}
+};
+
+// The same transform on pencils owned by the calling warp (all 32 lanes call
+// it; only __syncwarp() between passes).
+template <int L, int DIR, int NP, int INNER, int BS, int ES, int TWL = kTwN, int P = 0,
+          bool DONE = (P >= npasses(L))>
+struct FftW;
+template <int L, int DIR, int NP, int INNER, int BS, int ES, int TWL, int P>
+struct FftW<L, DIR, NP, INNER, BS, ES, TWL, P, false> {
+  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw,
+                                             const float2* __restrict__ pre = nullptr) {
+    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, 32, INNER, BS, ES, TWL, true>(s, tw,
+                                                                                          P == 0 ? pre : nullptr);
+    FftW<L, DIR, NP, INNER, BS, ES, TWL, P + 1>::run(s, tw);
+  }
+};
+template <int L, int DIR, int NP, int INNER, int BS, int ES, int TWL, int P>
+struct FftW<L, DIR, NP, INNER, BS, ES, TWL, P, true> {
   __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr) {}
 };
 

@@ -155,6 +155,171 @@ __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ 
   }
 }
 
+// Kernel multiply at the points (j, l) of columns j0 .. j0 + YW - 1 of the
+// plane (NTH threads, thread index tid): frequency (ky, kz) = (CLY j + ry,
+// CLZ l + rz); ktf holds the octant per kx plane, ky fastest
+// (ktf[kx][c][iz][iy]); mirror signs: Nxy odd in y, Nxz odd in z, Nyz odd in
+// both.  The coefficient loads of CH points are issued together.
+template <int LY, int LZ, int RP, int CS, int YW, int NTH, int CHMAX>
+__device__ __forceinline__ void kernel_mul(float2* s, const float* __restrict__ kt, const Geom& g, int kx, int ry,
+                                           int rz, int j0, int tid) {
+  constexpr int PW = YW * LZ;
+  constexpr int PPT = (PW + NTH - 1) / NTH;   // points per thread
+  constexpr int CH = PPT < CHMAX ? PPT : CHMAX;
+  const long long per = (long long)g.hky * g.hkz;
+#pragma unroll
+  for (int q0 = 0; q0 < PPT; q0 += CH) {
+    float kc[CH][6];
+    float sgn[CH][2];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int e = tid + (q0 + q) * NTH;
+      if (e >= PW) continue;
+      const int j = j0 + e % YW, l = e / YW;
+      const int ky = g.cly * j + ry, kz = g.clz * l + rz;
+      int iy = ky, iz = kz;
+      float sy = 1.f, sz = 1.f;
+      if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
+      if (kz > g.pz / 2) { iz = g.pz - kz; sz = -1.f; }
+      const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) kc[q][t] = __ldg(&kt[t * per + o]);
+      sgn[q][0] = sy;
+      sgn[q][1] = sz;
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int e = tid + (q0 + q) * NTH;
+      if (e >= PW) continue;
+      const int j = j0 + e % YW, l = e / YW;
+      const int a = l * RP + j;
+      const float kxx = kc[q][0], kyy = kc[q][1], kzz = kc[q][2];
+      const float kxy = sgn[q][0] * kc[q][3], kxz = sgn[q][1] * kc[q][4], kyz = sgn[q][0] * sgn[q][1] * kc[q][5];
+      const float2 X = s[a], Y = s[CS + a], Z = s[2 * CS + a];
+      s[a] = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+      s[CS + a] = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+      s[2 * CS + a] = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+    }
+  }
+}
+
+// radix of the last forward / first inverse z pass in z_mid (4 at most, so
+// that three components and their kernel coefficients fit in registers)
+__host__ __device__ constexpr int zmid_radix(int lz) { return lz >= 4 ? 4 : lz; }
+
+// The middle of the z transforms of all three components, fused (LZ =
+// R0 R1 with R1 = zmid_radix(LZ) the radix of the last forward pass, R0 = 1
+// for one pass):
+// for butterfly j of column p it runs the last forward pass on the R1
+// values at z = j + R0 r, multiplies the three components by the kernel at
+// those R1 frequencies and runs the first inverse pass (radix R1, no
+// twiddle), writing back to the positions it read -- so butterflies never
+// touch each other's data and need no barrier.  The standard first inverse
+// pass would store output r of butterfly j at j R1 + r; z_inv_tail reads
+// that transposed order.
+template <int LY, int LZ, int NT, int RP, int CS>
+__device__ __forceinline__ void z_mid(float2* s, const float2* __restrict__ twz, const float2* __restrict__ rtz,
+                                      const float* __restrict__ kt, const Geom& g, int kx, int ry, int rz) {
+  constexpr int R1 = zmid_radix(LZ);
+  constexpr int R0 = LZ / R1;
+  constexpr int TOT = R0 * LY;
+  constexpr int PER = (TOT + NT - 1) / NT;
+  const long long per = (long long)g.hky * g.hkz;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * NT;
+    if (TOT % NT != 0 && b >= TOT) continue;
+    const int p = b % LY, j = b / LY;
+    const int ky = g.cly * p + ry;
+    int iy = ky;
+    float sy = 1.f;
+    if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
+    float kc[R1][6], sz[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int kz = g.clz * (j + R0 * r) + rz;
+      int iz = kz;
+      sz[r] = 1.f;
+      if (kz > g.pz / 2) { iz = g.pz - kz; sz[r] = -1.f; }
+      const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) kc[r][t] = __ldg(&kt[t * per + o]);
+    }
+    float2 v[3][R1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[c][r] = s[c * CS + (j + R0 * r) * RP + p];
+    if (R0 == 1) {
+      if (rz) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int r = 0; r < R1; ++r) v[c][r] = cmul(v[c][r], rtz[r]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 1; r < R1; ++r) v[c][r] = cmul(v[c][r], twz[(r * j) & (LZ - 1)]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Dft<R1, -1>::run(v[c]);
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const float kxx = kc[r][0], kyy = kc[r][1], kzz = kc[r][2];
+      const float kxy = sy * kc[r][3], kxz = sz[r] * kc[r][4], kyz = sy * sz[r] * kc[r][5];
+      const float2 X = v[0][r], Y = v[1][r], Z = v[2][r];
+      v[0][r] = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+      v[1][r] = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+      v[2][r] = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Dft<R1, 1>::run(v[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) s[c * CS + (j + R0 * r) * RP + p] = v[c][r];
+  }
+}
+
+// Second (last) inverse z pass of one component after z_mid: radix R0,
+// butterfly j2 < R1 reads element r2 at the transposed position r2 + R0 j2
+// and writes the natural order j2 + R1 r2.  Ends with __syncthreads().
+template <int LY, int LZ, int NT, int RP>
+__device__ __forceinline__ void z_inv_tail(float2* sc, const float2* __restrict__ twz) {
+  constexpr int R1 = zmid_radix(LZ);
+  constexpr int R0 = LZ / R1;
+  if constexpr (R0 > 1) {
+    constexpr int TOT = R1 * LY;
+    constexpr int PER = (TOT + NT - 1) / NT;
+    float2 v[PER][R0];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int b = threadIdx.x + q * NT;
+      if (TOT % NT == 0 || b < TOT) {
+        const int p = b % LY, j2 = b / LY;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[q][r] = sc[(r + R0 * j2) * RP + p];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int b = threadIdx.x + q * NT;
+      if (TOT % NT == 0 || b < TOT) {
+        const int p = b % LY, j2 = b / LY;
+#pragma unroll
+        for (int r = 1; r < R0; ++r) v[q][r] = cmul(v[q][r], cconj(twz[(r * j2) & (LZ - 1)]));
+        Dft<R0, 1>::run(v[q]);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) sc[(j2 + R1 * r) * RP + p] = v[q][r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // ----------------------------------------------------------------------------
 // k_yz: plane [3][LZ][LY] in shared memory, y fastest, rows padded to an
 // odd pitch RP = LY + 1 (conflict-free row and column transforms)
@@ -203,59 +368,30 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   }
   asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
-  // 2. forward transforms along y (LZ rows) and z (LY columns), one
-  //    component at a time; the class twiddle exp(-2 pi i (y ry / py +
-  //    z rz / pz)) is applied as the first pass loads its inputs
-  for (int c = 0; c < 3; ++c) {
-    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
-    FftG<LZ, -1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz, rz ? rtz : nullptr);
-  }
-  // 3. multiply by the kernel at (kx, ky = CLY j + ry, kz = CLZ l + rz);
-  //    (ktf holds the octant per kx plane, ky fastest: ktf[kx][c][iz][iy];
-  //    mirror signs: Nxy odd in y, Nxz odd in z, Nyz odd in both); the
-  //    coefficient loads of CH points are issued together
-  constexpr int PPT = (PL + NT - 1) / NT;   // points per thread
-  constexpr int CH = PPT < 2 ? PPT : 2;
-#pragma unroll
-  for (int q0 = 0; q0 < PPT; q0 += CH) {
-    float kc[CH][6];
-    float sgn[CH][2];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int e = threadIdx.x + (q0 + q) * NT;
-      if (e >= PL) continue;
-      const int j = e % LY, l = e / LY;
-      const int ky = g.cly * j + ry, kz = g.clz * l + rz;
-      int iy = ky, iz = kz;
-      float sy = 1.f, sz = 1.f;
-      if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
-      if (kz > g.pz / 2) { iz = g.pz - kz; sz = -1.f; }
-      const long long per = (long long)g.hky * g.hkz;
-      const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
-#pragma unroll
-      for (int t = 0; t < 6; ++t) kc[q][t] = __ldg(&kt[t * per + o]);
-      sgn[q][0] = sy;
-      sgn[q][1] = sz;
+  // 2. forward transforms along y (LZ rows) and the first z pass (LY
+  //    columns), one component at a time; the class twiddle exp(-2 pi i
+  //    (y ry / py + z rz / pz)) is applied as the first pass loads its inputs
+  if constexpr (LZ > 1) {
+    constexpr int R0 = LZ / zmid_radix(LZ);
+    for (int c = 0; c < 3; ++c) {
+      FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
+      if constexpr (R0 > 1)
+        stockham_pass<LZ, R0, 1, -1, LY, NT, LY, CS, RP, LZ>(s + c * CS, twz, rz ? rtz : nullptr);
     }
-#pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int e = threadIdx.x + (q0 + q) * NT;
-      if (e >= PL) continue;
-      const int j = e % LY, l = e / LY;
-      const int a = l * RP + j;
-      const float kxx = kc[q][0], kyy = kc[q][1], kzz = kc[q][2];
-      const float kxy = sgn[q][0] * kc[q][3], kxz = sgn[q][1] * kc[q][4], kyz = sgn[q][0] * sgn[q][1] * kc[q][5];
-      const float2 X = s[a], Y = s[CS + a], Z = s[2 * CS + a];
-      s[a] = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
-      s[CS + a] = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
-      s[2 * CS + a] = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+    // 3. last forward z pass, kernel multiply at (kx, ky = CLY j + ry,
+    //    kz = CLZ l + rz), first inverse z pass, all in registers
+    z_mid<LY, LZ, NT, RP, CS>(s, twz, rtz, kt, g, kx, ry, rz);
+    __syncthreads();
+    // 4. rest of the inverse transforms
+    for (int c = 0; c < 3; ++c) {
+      z_inv_tail<LY, LZ, NT, RP>(s + c * CS, twz);
+      FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
     }
-  }
-  __syncthreads();
-  // 4. inverse transforms
-  for (int c = 0; c < 3; ++c) {
-    FftG<LZ, 1, LY, NT, LY, CS, RP, LZ>::run(s + c * CS, twz);
-    FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
+  } else {
+    for (int c = 0; c < 3; ++c) FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
+    kernel_mul<LY, LZ, RP, CS, LY, NT, 2>(s, kt, g, kx, ry, rz, 0, threadIdx.x);
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
   }
   // 5. sum the class contributions across the cluster, each multiplied by
   //    the conjugate of its class twiddle; each block stores one contiguous
@@ -281,24 +417,53 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   if (CL > 1) cluster.sync();   // keep shared memory alive until every peer has read it
 }
 
+// rows per block of the x-row kernels: the default rule (enough blocks to
+// fill the GPU: 8 rows of <= 128 points), or half / twice it
 template <int L>
 struct RowCfgT {
-  // enough blocks to fill the GPU: 8 rows of <= 128 points per block
   static constexpr int ROWS = L >= 512 ? 2 : (L >= 256 ? 4 : 8);
+  static constexpr int RH = ROWS > 1 ? ROWS / 2 : 1;
+  static constexpr int R2 = 2 * ROWS;
+};
+template <int L, int ROWS>
+struct RowNT {
   static constexpr int NT = ROWS * L / 8 < 64 ? 64 : ROWS * L / 8;
 };
 
+template <int L, int ROWS>
+void run_fx_rows(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
+  constexpr int NT = RowNT<L, ROWS>::NT;
+  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz, 3 * ba.count);
+  k_fx_t<L, ROWS, NT><<<grid, NT, 0, s>>>(g, m, b.mask, b.region, b.lut, b.spec, b.tw, b.st, ba);
+}
+template <int L, int ROWS>
+void run_ix_rows(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
+  constexpr int NT = RowNT<L, ROWS>::NT;
+  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz, 3 * ba.count);
+  k_ix_t<L, ROWS, NT><<<grid, NT, 0, s>>>(g, b.spec, b.bd, b.tw, b.st, ba);
+}
 template <int L>
 void run_fx_t(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
   using C = RowCfgT<L>;
-  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3 * ba.count);
-  k_fx_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, m, b.mask, b.region, b.lut, b.spec, b.tw, b.st, ba);
+  if (g.xrows == C::RH && C::RH != C::ROWS) run_fx_rows<L, C::RH>(g, b, m, s, ba);
+  else if (g.xrows == C::R2) run_fx_rows<L, C::R2>(g, b, m, s, ba);
+  else run_fx_rows<L, C::ROWS>(g, b, m, s, ba);
 }
 template <int L>
 void run_ix_t(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
   using C = RowCfgT<L>;
-  dim3 grid((g.ny + C::ROWS - 1) / C::ROWS, g.nz, 3 * ba.count);
-  k_ix_t<L, C::ROWS, C::NT><<<grid, C::NT, 0, s>>>(g, b.spec, b.bd, b.tw, b.st, ba);
+  if (g.xrows == C::RH && C::RH != C::ROWS) run_ix_rows<L, C::RH>(g, b, s, ba);
+  else if (g.xrows == C::R2) run_ix_rows<L, C::R2>(g, b, s, ba);
+  else run_ix_rows<L, C::ROWS>(g, b, s, ba);
+}
+template <int L>
+int xrow_options(int* out) {
+  using C = RowCfgT<L>;
+  int n = 0;
+  if (C::RH != C::ROWS) out[n++] = C::RH;
+  out[n++] = C::ROWS;
+  out[n++] = C::R2;
+  return n;
 }
 
 template <int LY, int LZ>
@@ -353,27 +518,6 @@ void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_
   k_kt_transpose<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, kt, ktf);
 }
 
-// Chooses the residue split for the fused path: py/cly >= ny, pz/clz >= nz,
-// 3 (py/cly)(pz/clz) complex values in at most 96 KB of shared memory.
-bool fused_plan(Geom& g) {
-  g.fused = 0;
-  if (g.px < 32 || g.lx > 512) return false;
-  for (int clz = 1; clz <= (g.pz > 1 ? 2 : 1); ++clz)
-    for (int cly = 1; cly <= (g.py > 1 ? 2 : 1); ++cly) {
-      const int ly = g.py / cly, lz = g.pz / clz;
-      if (ly < g.ny || lz < g.nz) continue;
-      if (ly < 16 || ly > 1024 || lz > 32) continue;
-      if ((long long)ly * lz > 4096) continue;
-      g.cly = cly;
-      g.clz = clz;
-      g.ly = ly;
-      g.lz = lz;
-      g.fused = 1;
-      return true;
-    }
-  return false;
-}
-
 #define MM_ROWL(LEN, CALL) \
   switch (LEN) {           \
     case 16: CALL(16); break; \
@@ -384,6 +528,56 @@ bool fused_plan(Geom& g) {
     case 512: CALL(512); break; \
     default: break;        \
   }
+
+// Residue splits for the fused path: py/cly >= ny, pz/clz >= nz,
+// 3 (py/cly)(pz/clz) complex values in at most 96 KB of shared memory,
+// clusters of at most 4 blocks; the smallest cluster first.
+int fused_splits(const Geom& g, int (*out)[2], int max) {
+  if (g.px < 32 || g.lx > 512) return 0;
+  int n = 0;
+  for (int clz = 1; clz <= (g.pz > 1 ? 2 : 1); ++clz)
+    for (int cly = 1; cly <= (g.py > 1 ? 2 : 1); ++cly) {
+      const int ly = g.py / cly, lz = g.pz / clz;
+      if (ly < g.ny || lz < g.nz) continue;
+      if (ly < 16 || ly > 1024 || lz > 32) continue;
+      if ((long long)ly * lz > 4096) continue;
+      if (n < max) {
+        out[n][0] = cly;
+        out[n][1] = clz;
+      }
+      ++n;
+    }
+  return n < max ? n : max;
+}
+
+void fused_set_split(Geom& g, int cly, int clz) {
+  g.cly = cly;
+  g.clz = clz;
+  g.ly = g.py / cly;
+  g.lz = g.pz / clz;
+  g.fused = 1;
+}
+
+int fused_xrows(const Geom& g, int* out, int max) {
+  int tmp[3];
+  int n = 0;
+#define XR(LL) n = xrow_options<LL>(tmp)
+  MM_ROWL(g.lx, XR)
+#undef XR
+  n = n < max ? n : max;
+  for (int i = 0; i < n; ++i) out[i] = tmp[i];
+  return n;
+}
+
+// The default plan: the first (smallest) split.
+bool fused_plan(Geom& g) {
+  g.fused = 0;
+  int sp[4][2];
+  if (fused_splits(g, sp, 4) == 0) return false;
+  fused_set_split(g, sp[0][0], sp[0][1]);
+  return true;
+}
+
 
 void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
   launch_demag_fused_batch(g, b, m, s, BatchArgs{1, nullptr, nullptr, 0});

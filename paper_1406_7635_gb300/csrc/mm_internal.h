@@ -43,6 +43,7 @@ struct Geom {
   // fused path (fft_fused.cu): spectrum laid out [3][hx][nz][ny], one
   // cluster of cly*clz blocks per kx plane, each transforming ly x lz points
   int fused, cly, clz, ly, lz;
+  int xrows;              // x-row kernels: rows per block (0 = default rule)
 };
 
 // Integrator state on the device (one per context).  Every kernel of a step
@@ -115,6 +116,13 @@ struct Geom;
 void launch_demag(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
 // fused three-kernel convolution; fused_plan() decides whether g supports it
 bool fused_plan(Geom& g);
+// tile choices of the fused convolution for g (an autotuner times them):
+// residue splits (cly, clz) that satisfy the plan's limits, and rows per
+// block of the x-row kernels; return the number written (at most max)
+int fused_splits(const Geom& g, int (*out)[2], int max);
+int fused_xrows(const Geom& g, int* out, int max);
+// applies a split chosen from fused_splits
+void fused_set_split(Geom& g, int cly, int clz);
 void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
 void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba);
 void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s);

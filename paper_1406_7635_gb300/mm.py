@@ -107,6 +107,7 @@ _SIGS = {
     "mm_batch_get_stats": (_I, [_P, _I, C.POINTER(mm_stats)]),
     "mm_batch_get_dt_history": (_I, [_P, _I, _P, _I, C.POINTER(_I)]),
     "mm_batch_num_classes": (_I, [_P]),
+    "mm_batch_class_info": (_I, [_P, _I, _P, C.POINTER(_D)]),
     "mm_fno_create": (_I, [C.POINTER(_P), _I, _I, C.POINTER(mm_fno_cfg), _I, _P]),
     "mm_fno_destroy": (_I, [_P]),
     "mm_fno_param_count": (C.c_longlong, [_P]),
@@ -413,6 +414,15 @@ class Batch:
         n = C.c_int()
         _check(mm_batch_get_dt_history(self.h, i, _ptr(out), max_n, C.byref(n)))
         return out[:n.value].copy()
+
+    def class_info(self, c):
+        """Autotuned FFT tiles of shape class c: grid, instances, residue
+        split, x rows per block and the chosen convolution time (us)."""
+        info = np.zeros(7, dtype=np.int32)
+        us = C.c_double()
+        _check(mm_batch_class_info(self.h, int(c), _ptr(info), C.byref(us)))
+        return {"grid": [int(info[0]), int(info[1]), int(info[2])], "instances": int(info[3]),
+                "cly": int(info[4]), "clz": int(info[5]), "xrows": int(info[6]), "conv_us": us.value}
 
     def num_classes(self):
         return mm_batch_num_classes(self.h)

@@ -31,6 +31,7 @@ def batch_run(mm):
     specs, m0s = batch_instances(16, shapes=SMALL_SHAPES, seed=77)
     b = mm.Batch(specs)
     assert b.num_classes() == len({(s["nx"], s["ny"], s["nz"]) for s in specs})
+    tiles = [b.class_info(c) for c in range(b.num_classes())]
     for i, m in enumerate(m0s):
         b.set_m(i, m)
     t_end = 4e-12
@@ -38,7 +39,7 @@ def batch_run(mm):
     out = {"specs": specs, "m0s": m0s, "t_end": t_end,
            "m": [b.get_m(i) for i in range(len(specs))],
            "dts": [b.get_dt_history(i) for i in range(len(specs))],
-           "stats": [b.get_stats(i) for i in range(len(specs))]}
+           "stats": [b.get_stats(i) for i in range(len(specs))], "tiles": tiles}
     b.close()
     return out
 
@@ -89,3 +90,28 @@ def test_batch_nonfinite_instance_reports_error(mm):
     assert b.get_stats(1)["status"] == -4
     assert b.get_stats(0)["status"] == 0
     b.close()
+
+
+def test_autotuned_tiles_are_valid(batch_run):
+    """The FFT-tile autotuner picks, per shape class, a residue split whose
+    class transform still holds the grid (py / cly >= ny, pz / clz >= nz, at
+    most 4096 points per block) and an x-row block size among the offered
+    ones, and reports the timed convolution; the instances then run with those
+    tiles (the parity tests above)."""
+    def pad(n):
+        return 1 if n == 1 else 1 << (2 * n - 2).bit_length()
+    seen = {(s["nx"], s["ny"], s["nz"]): 0 for s in batch_run["specs"]}
+    for s in batch_run["specs"]:
+        seen[(s["nx"], s["ny"], s["nz"])] += 1
+    assert len(batch_run["tiles"]) == len(seen)
+    for t in batch_run["tiles"]:
+        nx, ny, nz = t["grid"]
+        assert seen[(nx, ny, nz)] == t["instances"]
+        py, pz = pad(ny), pad(nz)
+        assert t["cly"] in (1, 2) and t["clz"] in (1, 2)
+        assert py // t["cly"] >= ny and pz // t["clz"] >= nz
+        assert (py // t["cly"]) * (pz // t["clz"]) <= 4096
+        lx = pad(nx) // 2
+        default = 2 if lx >= 512 else (4 if lx >= 256 else 8)
+        assert t["xrows"] in (max(default // 2, 1), default, 2 * default)
+        assert t["conv_us"] > 0
