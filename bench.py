@@ -36,6 +36,23 @@ DEFAULT_WORKLOAD = "ellipsoid_128x128x32"
 SIDE_WORKLOAD = "grains_256x256x1"
 
 
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' values of x (a time): every rank gets it.
+    Replicas share nothing else; this is the only collective of a run."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Weak-scaling aggregate: the units every rank processed divided by the
+    slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -230,16 +247,12 @@ def run_ours(args, rank, world, local_rank):
         return p, ctx, dev_s, s0, s1, clk
 
     def reduce_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, world, dev)
 
     K, W = args.steps, args.warmup
     p, ctx, dev_s, s0, s1, clk = bench_workload(args.workload, K, W)
     t_max = reduce_max(dev_s)
-    value = p.ncells * K * world / t_max
+    value = whole_job_rate(p.ncells * K, world, t_max)
     attempts = (s1["accepted"] + s1["rejected"]) - (s0["accepted"] + s0["rejected"])
     launches = s1["launches"] - s0["launches"]
 

@@ -356,12 +356,16 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   const int kx = (blockIdx.x / CL) % g.hx;
   // 1. load the plane (asynchronous copies, all in flight at once); rows and
   //    columns past the grid are zero
+  // (32-bit offsets: one instance's spectrum, 3 hx nz ny < 2^31 points)
+  const int cstride = g.hx * g.nz * g.ny;              // component stride of spec
+  float2* const plane = spec + kx * g.nz * g.ny;       // this kx plane, component 0
   for (int e = threadIdx.x; e < 3 * PL; e += NT) {
     const int y = e % LY, z = (e / LY) % LZ, c = e / PL;
     float2* dst = s + c * CS + z * RP + y;
     if (y < g.ny && z < g.nz) {
       const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(spec + tidx(g, c, kx, z, y)));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr),
+                   "l"(plane + c * cstride + z * g.ny + y));
     } else {
       *dst = make_float2(0.f, 0.f);
     }
@@ -398,21 +402,45 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   //    1/CL share of the plane
   if (CL > 1) cluster.sync();
   else __syncthreads();
-  const int nout = 3 * g.nz * g.ny;
-  const int chunk = (nout + CL - 1) / CL;
-  const int o_end = min(nout, (rank + 1) * chunk);
-  for (int o = rank * chunk + threadIdx.x; o < o_end; o += NT) {
-    const int y = o % g.ny, z = (o / g.ny) % g.nz, c = o / (g.ny * g.nz);
-    const int e = c * CS + z * RP + y;
-    const float2 ty = cconj(rty[y]), tz = cconj(rtz[z]), tyz = cmul(ty, tz);
-    float2 v = make_float2(0.f, 0.f);
-    for (int q = 0; q < CL; ++q) {
-      const float2 val = q == rank ? s[e] : cluster.map_shared_rank(s, q)[e];
-      const int qy = q % g.cly, qz = q / g.cly;
-      const float2 w = qy ? (qz ? tyz : ty) : (qz ? tz : make_float2(1.f, 0.f));
-      v = cadd(v, (qy || qz) ? cmul(val, w) : val);
+  // output points o = (c LZ + z) LY + y of the padded class plane (points
+  // with z >= nz or y >= ny are skipped); each block takes 1/CL of them
+  constexpr int NOUT = 3 * PL;
+  const int chunk = (NOUT + CL - 1) / CL;
+  const int o_end = min(NOUT, (rank + 1) * chunk);
+  // the (at most 4) blocks' planes; a batch of RB points per thread issues
+  // all its distributed-shared-memory loads before combining them
+  const float2* part[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) part[q] = (q < CL && q != rank) ? cluster.map_shared_rank(s, q) : s;
+  constexpr int RB = 3;
+  for (int ob = rank * chunk + threadIdx.x; ob < o_end; ob += RB * NT) {
+    float2 val[RB][4];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int o = ob + u * NT;
+      const int y = o % LY, z = (o / LY) % LZ, c = o / PL;
+      if (o >= o_end || y >= g.ny || z >= g.nz) continue;
+      const int e = c * CS + z * RP + y;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < CL) val[u][q] = part[q][e];
     }
-    spec[tidx(g, c, kx, z, y)] = v;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int o = ob + u * NT;
+      const int y = o % LY, z = (o / LY) % LZ, c = o / PL;
+      if (o >= o_end || y >= g.ny || z >= g.nz) continue;
+      const float2 ty = cconj(rty[y]), tz = cconj(rtz[z]), tyz = cmul(ty, tz);
+      float2 v = val[u][0];   // class (0, 0): no twiddle
+#pragma unroll
+      for (int q = 1; q < 4; ++q) {
+        if (q >= CL) continue;
+        const int qy = q % g.cly, qz = q / g.cly;
+        const float2 w = qy ? (qz ? tyz : ty) : tz;
+        v = cadd(v, cmul(val[u][q], w));
+      }
+      plane[c * cstride + z * g.ny + y] = v;
+    }
   }
   if (CL > 1) cluster.sync();   // keep shared memory alive until every peer has read it
 }

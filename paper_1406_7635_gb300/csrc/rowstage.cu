@@ -24,8 +24,9 @@ enum { ROW_K1 = 0, ROW_NEXT = 1, ROW_LAST = 2 };
 
 __device__ __forceinline__ float* stage_buf(const Buffers& b, int s) { return (s & 1) ? b.ms2 : b.ms; }
 
-__device__ __forceinline__ long long tix(const Geom& g, int c, int kx, int z, int y) {
-  return (((long long)c * g.hx + kx) * g.nz + z) * g.ny + y;
+// 32-bit indices: the fused layout has nz <= 32 and at most 2^28 cells
+__device__ __forceinline__ int tix(const Geom& g, int c, int kx, int z, int y) {
+  return ((c * g.hx + kx) * g.nz + z) * g.ny + y;
 }
 
 // x R2C of the packed rows in s (3 * ROWS pencils) into the spectrum
@@ -71,19 +72,19 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
     const int x = e % (2 * L), r = e / (2 * L), y = y0 + r;
     float v[3] = {0.f, 0.f, 0.f};
     if (y < g.ny && x < g.nx) {
-      const long long i = ((long long)z * g.ny + y) * g.nx + x;
-      float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
+      const int n = (int)g.n, i = (z * g.ny + y) * g.nx + x;
+      float a0 = m[i], a1 = m[n + i], a2 = m[2 * n + i];
       for (int j = 0; j < s; ++j) {
         const float a = sc->ah[s][j];
         if (a == 0.0f) continue;
         const float* __restrict__ k = pick_k(p, k_role(j, par));
         a0 = fmaf(a, k[i], a0);
-        a1 = fmaf(a, k[g.n + i], a1);
-        a2 = fmaf(a, k[2 * g.n + i], a2);
+        a1 = fmaf(a, k[n + i], a1);
+        a2 = fmaf(a, k[2 * n + i], a2);
       }
       out[i] = a0;
-      out[g.n + i] = a1;
-      out[2 * g.n + i] = a2;
+      out[n + i] = a1;
+      out[2 * n + i] = a2;
       const int ci = b.code[i];
       const float ms = ci != kVacuum ? __ldg(&b.lut->msat[ci]) : 0.f;
       v[0] = ms * a0;
@@ -115,6 +116,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
@@ -127,23 +132,38 @@ __device__ __forceinline__ void stage_stencil(const Geom& g, const float* __rest
                                               float* sten, int* scode, int y0, int z) {
   constexpr int NR = RsSmem<L, ROWS>::NR;
   const bool vec = (g.nx & 3) == 0;      // rows start on 16-byte boundaries
-  const int w = vec ? 4 : 1;
-  const int cpr = (g.nx + w - 1) / w;
-  const int total = NR * 4 * cpr;
-  for (int e = threadIdx.x; e < total; e += NT) {
-    const int ch = e % cpr, t = e / cpr, a = t & 3, lr = t >> 2;
-    int yy = y0 + lr - 1, zz = z;
-    if (lr >= ROWS + 2) {
-      const int q = lr - (ROWS + 2);
-      yy = y0 + (q % ROWS);
-      zz = q < ROWS ? z - 1 : z + 1;
+  const int n = (int)g.n;
+  if (vec) {
+    constexpr int CPR = L / 4;             // 16-byte chunks per (padded) row
+    for (int e = threadIdx.x; e < NR * 4 * CPR; e += NT) {
+      const int ch = e % CPR, t = e / CPR, a = t & 3, lr = t >> 2;
+      int yy = y0 + lr - 1, zz = z;
+      if (lr >= ROWS + 2) {
+        const int q = lr - (ROWS + 2);
+        yy = y0 + (q % ROWS);
+        zz = q < ROWS ? z - 1 : z + 1;
+      }
+      if (4 * ch >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
+      const int row = (zz * g.ny + yy) * g.nx + 4 * ch;
+      const void* src = a < 3 ? (const void*)(ms + a * n + row) : (const void*)(code + row);
+      void* dst = a < 3 ? (void*)(sten + (a * NR + lr) * L + 4 * ch) : (void*)(scode + lr * L + 4 * ch);
+      cp_async16(dst, src);
     }
-    if (yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
-    const long long row = ((long long)zz * g.ny + yy) * g.nx + (long long)ch * w;
-    const void* src = a < 3 ? (const void*)(ms + a * g.n + row) : (const void*)(code + row);
-    void* dst = a < 3 ? (void*)(sten + (a * NR + lr) * L + ch * w) : (void*)(scode + lr * L + ch * w);
-    if (vec) cp_async16(dst, src);
-    else cp_async4(dst, src);
+  } else {
+    for (int e = threadIdx.x; e < NR * 4 * L; e += NT) {
+      const int ch = e % L, t = e / L, a = t & 3, lr = t >> 2;
+      int yy = y0 + lr - 1, zz = z;
+      if (lr >= ROWS + 2) {
+        const int q = lr - (ROWS + 2);
+        yy = y0 + (q % ROWS);
+        zz = q < ROWS ? z - 1 : z + 1;
+      }
+      if (ch >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
+      const int row = (zz * g.ny + yy) * g.nx + ch;
+      const void* src = a < 3 ? (const void*)(ms + a * n + row) : (const void*)(code + row);
+      void* dst = a < 3 ? (void*)(sten + (a * NR + lr) * L + ch) : (void*)(scode + lr * L + ch);
+      cp_async4(dst, src);
+    }
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -158,6 +178,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   // real cells per thread: ROWS rows of at most L cells (nx <= 2L, and the
   // x-padding cells are not visited)
   constexpr int CPT = (ROWS * L + NT - 1) / NT;
+  constexpr int NCELL = ROWS * L;   // cell slots: x < L of each row (x >= nx idle)
   extern __shared__ float4 rs_dyn[];
   float2* sm = reinterpret_cast<float2*>(rs_dyn);
   float* sten = reinterpret_cast<float*>(reinterpret_cast<char*>(rs_dyn) + SM::SPEC);
@@ -166,15 +187,21 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   __shared__ float wmax[32];
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
   const float* __restrict__ ms = stage_buf(b, s);
-  // 0. stencil rows of the stage input arrive while the x transform runs
-  stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
-  load_tables<L, NT>(twl, tw2, b.tw);
-  // 1. x C2R of the demag spectrum rows (3 components)
+  // 0. asynchronous copies: the demag spectrum rows (first group), then the
+  //    stencil rows of the stage input (second group, awaited only after the
+  //    x transform)
   for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
     const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
     const int y = y0 + r;
-    sm[(c * ROWS + r) * PST + k] = y < g.ny ? b.spec[tix(g, c, k, z, y)] : make_float2(0.f, 0.f);
+    float2* dst = sm + (c * ROWS + r) * PST + k;
+    if (y < g.ny) cp_async8(dst, b.spec + tix(g, c, k, z, y));
+    else *dst = make_float2(0.f, 0.f);
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
+  load_tables<L, NT>(twl, tw2, b.tw);
+  // 1. x C2R of the demag spectrum rows (3 components)
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
   __syncthreads();
   for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
     const int pen = e / (L / 2 + 1), k = e % (L / 2 + 1);
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   FftG<L, 1, 3 * ROWS, NT, 1, PST, 1, L>::run(sm, twl);
   const int par = st->parity;
   const float* __restrict__ m = par ? p.m1 : p.m0;
-  const int ncell = ROWS * g.nx;
+  const int n = (int)g.n;
   // 2. sums over the earlier stages at the block's cells (global streams):
   //    next stage m + dt sum_j a_{s+1,j} k_j, or the error sum dt sum_j e_j k_j
   float av[CPT][3];
@@ -206,19 +233,19 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   for (int q = 0; q < CPT; ++q) {
     const int e = threadIdx.x + q * NT;
     av[q][0] = av[q][1] = av[q][2] = 0.f;
-    if (mode == ROW_K1 || e >= ncell) continue;
-    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
-    if (y >= g.ny) continue;
-    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    if (mode == ROW_K1 || e >= NCELL) continue;
+    const int x = e % L, r = e / L, y = y0 + r;
+    if (x >= g.nx || y >= g.ny) continue;
+    const int i = (z * g.ny + y) * g.nx + x;
     if (mode == ROW_NEXT) {
-      float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
+      float a0 = m[i], a1 = m[n + i], a2 = m[2 * n + i];
       for (int j = 0; j < s; ++j) {
         const float a = sc->ah[s + 1][j];
         if (a == 0.0f) continue;
         const float* __restrict__ k = pick_k(p, k_role(j, par));
         a0 = fmaf(a, k[i], a0);
-        a1 = fmaf(a, k[g.n + i], a1);
-        a2 = fmaf(a, k[2 * g.n + i], a2);
+        a1 = fmaf(a, k[n + i], a1);
+        a2 = fmaf(a, k[2 * n + i], a2);
       }
       av[q][0] = a0;
       av[q][1] = a1;
@@ -230,8 +257,8 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
         if (c == 0.0f) continue;
         const float* __restrict__ k = pick_k(p, k_role(j, par));
         ex = fmaf(c, k[i], ex);
-        ey = fmaf(c, k[g.n + i], ey);
-        ez = fmaf(c, k[2 * g.n + i], ez);
+        ey = fmaf(c, k[n + i], ey);
+        ez = fmaf(c, k[2 * n + i], ez);
       }
       av[q][0] = ex;
       av[q][1] = ey;
@@ -253,9 +280,9 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     kv[q][0] = kv[q][1] = kv[q][2] = 0.f;
     mv[q][0] = mv[q][1] = mv[q][2] = 0.f;
     cv[q] = kVacuum;
-    if (e >= ncell) continue;
-    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
-    if (y >= g.ny) continue;
+    if (e >= NCELL) continue;
+    const int x = e % L, r = e / L, y = y0 + r;
+    if (x >= g.nx || y >= g.ny) continue;
     const int C = (r + 1) * L + x;
     const int ci = scode[C];
     cv[q] = ci;
@@ -298,13 +325,13 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int e = threadIdx.x + q * NT;
-    if (e >= ncell) continue;
-    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
-    if (y >= g.ny) continue;
-    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    if (e >= NCELL) continue;
+    const int x = e % L, r = e / L, y = y0 + r;
+    if (x >= g.nx || y >= g.ny) continue;
+    const int i = (z * g.ny + y) * g.nx + x;
     kout[i] = kv[q][0];
-    kout[g.n + i] = kv[q][1];
-    kout[2 * g.n + i] = kv[q][2];
+    kout[n + i] = kv[q][1];
+    kout[2 * n + i] = kv[q][2];
   }
   if (mode == ROW_K1) return;
   if (mode == ROW_NEXT) {
@@ -321,16 +348,16 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int e = threadIdx.x + q * NT;
-      if (e >= ncell) continue;
-      const int x = e % g.nx, r = e / g.nx, y = y0 + r;
-      if (y >= g.ny) continue;
-      const long long i = ((long long)z * g.ny + y) * g.nx + x;
+      if (e >= NCELL) continue;
+      const int x = e % L, r = e / L, y = y0 + r;
+      if (x >= g.nx || y >= g.ny) continue;
+      const int i = (z * g.ny + y) * g.nx + x;
       const float n0 = fmaf(a, kv[q][0], av[q][0]);
       const float n1 = fmaf(a, kv[q][1], av[q][1]);
       const float n2 = fmaf(a, kv[q][2], av[q][2]);
       nxt[i] = n0;
-      nxt[g.n + i] = n1;
-      nxt[2 * g.n + i] = n2;
+      nxt[n + i] = n1;
+      nxt[2 * n + i] = n2;
       const float msat = cv[q] != kVacuum ? __ldg(&lut->msat[cv[q]]) : 0.f;
       sw[2 * (0 * ROWS + r) * PST + x] = msat * n0;
       sw[2 * (1 * ROWS + r) * PST + x] = msat * n1;
@@ -347,10 +374,10 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
 #pragma unroll
   for (int q = 0; q < CPT; ++q) {
     const int e = threadIdx.x + q * NT;
-    if (e >= ncell) continue;
-    const int x = e % g.nx, r = e / g.nx, y = y0 + r;
-    if (y >= g.ny) continue;
-    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    if (e >= NCELL) continue;
+    const int x = e % L, r = e / L, y = y0 + r;
+    if (x >= g.nx || y >= g.ny) continue;
+    const int i = (z * g.ny + y) * g.nx + x;
     if (cv[q] != kVacuum) {
       const float ex = fmaf(e6, kv[q][0], av[q][0]);
       const float ey = fmaf(e6, kv[q][1], av[q][1]);
@@ -361,10 +388,10 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       const float mx = mv[q][0], my = mv[q][1], mz = mv[q][2];
       const float inv = rsqrtf(mx * mx + my * my + mz * mz);
       mnew[i] = mx * inv;
-      mnew[g.n + i] = my * inv;
-      mnew[2 * g.n + i] = mz * inv;
+      mnew[n + i] = my * inv;
+      mnew[2 * n + i] = mz * inv;
     } else {
-      mnew[i] = mnew[g.n + i] = mnew[2 * g.n + i] = 0.0f;
+      mnew[i] = mnew[n + i] = mnew[2 * n + i] = 0.0f;
     }
   }
   for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
