@@ -106,23 +106,25 @@ __global__ void k_b_stage_input(Geom g, BPtrs p, float* __restrict__ ms, const I
   const int inst = blockIdx.y;
   const InstState& S = st[inst];
   if (S.done) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // in-instance offsets: 3 n < 2^31
   if (i >= g.n) return;
   const long long o = (long long)inst * 3 * g.n;
+  const int n = (int)g.n;
   const int par = S.parity;
   const float* __restrict__ m = (par ? p.m1 : p.m0) + o;
-  float a0 = m[i], a1 = m[g.n + i], a2 = m[2 * g.n + i];
+  float a0 = m[i], a1 = m[n + i], a2 = m[2 * n + i];
   for (int j = 0; j < s; ++j) {
     const float a = S.ah[s][j];
     if (a == 0.0f) continue;
     const float* __restrict__ k = bpick(p, role(j, par)) + o;
     a0 = fmaf(a, k[i], a0);
-    a1 = fmaf(a, k[g.n + i], a1);
-    a2 = fmaf(a, k[2 * g.n + i], a2);
+    a1 = fmaf(a, k[n + i], a1);
+    a2 = fmaf(a, k[2 * n + i], a2);
   }
-  ms[o + i] = a0;
-  ms[o + g.n + i] = a1;
-  ms[o + 2 * g.n + i] = a2;
+  float* __restrict__ mso = ms + o;
+  mso[i] = a0;
+  mso[n + i] = a1;
+  mso[2 * n + i] = a2;
 }
 
 // effective field (demag + exchange + static Zeeman) and LL torque
@@ -131,21 +133,23 @@ __global__ void k_b_torque(Geom g, BPtrs p, const float* __restrict__ ms, const 
   const int inst = blockIdx.y;
   const InstState& S = st[inst];
   if (S.done) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // in-instance offsets: 3 n < 2^31
   if (i >= g.n) return;
   const long long o = (long long)inst * 3 * g.n;
+  const int n = (int)g.n;
   const float* __restrict__ m = ms + o;
+  const float* __restrict__ bdo = bd + o;
   const InstParams P = prm[inst];
-  const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
-  const float mx = m[i], my = m[g.n + i], mz = m[2 * g.n + i];
-  float bx = bd[o + i] + P.b[0], by = bd[o + g.n + i] + P.b[1], bz = bd[o + 2 * g.n + i] + P.b[2];
-  auto nb = [&](long long j, float id2) {
+  const int x = i % g.nx, y = (i / g.nx) % g.ny, z = i / (g.nx * g.ny);
+  const float mx = m[i], my = m[n + i], mz = m[2 * n + i];
+  float bx = bdo[i] + P.b[0], by = bdo[n + i] + P.b[1], bz = bdo[2 * n + i] + P.b[2];
+  auto nb = [&](int j, float id2) {
     const float c = P.exch * id2;
     bx += c * (m[j] - mx);
-    by += c * (m[g.n + j] - my);
-    bz += c * (m[2 * g.n + j] - mz);
+    by += c * (m[n + j] - my);
+    bz += c * (m[2 * n + j] - mz);
   };
-  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  const int sy = g.nx, sz = g.nx * g.ny;
   if (x > 0) nb(i - 1, g.idx2);
   if (x < g.nx - 1) nb(i + 1, g.idx2);
   if (y > 0) nb(i - sy, g.idy2);
@@ -156,8 +160,8 @@ __global__ void k_b_torque(Geom g, BPtrs p, const float* __restrict__ ms, const 
   const float dx = my * cz - mz * cy, dy = mz * cx - mx * cz, dz = mx * cy - my * cx;
   float* __restrict__ k = bpick(p, role(s, S.parity)) + o;
   k[i] = P.gfac * (cx + P.alpha * dx);
-  k[g.n + i] = P.gfac * (cy + P.alpha * dy);
-  k[2 * g.n + i] = P.gfac * (cz + P.alpha * dz);
+  k[n + i] = P.gfac * (cy + P.alpha * dy);
+  k[2 * n + i] = P.gfac * (cz + P.alpha * dz);
 }
 
 // Sec. IV controller, per instance (the same readings as the single path).
@@ -200,28 +204,30 @@ __global__ void k_b_error(Geom g, BPtrs p, const float* __restrict__ ms, InstSta
   const int inst = blockIdx.y;
   InstState& S = st[inst];
   if (S.done) return;   // uniform over the instance's blocks
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // in-instance offsets: 3 n < 2^31
   const long long o = (long long)inst * 3 * g.n;
+  const int n = (int)g.n;
   const int par = S.parity;
   float e = 0.0f;
-  if (i < g.n) {
+  if (i < n) {
     float ex = 0.f, ey = 0.f, ez = 0.f;
     for (int j = 0; j < 7; ++j) {
       const float c = S.eh[j];
       if (c == 0.0f) continue;
       const float* __restrict__ k = bpick(p, role(j, par)) + o;
       ex = fmaf(c, k[i], ex);
-      ey = fmaf(c, k[g.n + i], ey);
-      ez = fmaf(c, k[2 * g.n + i], ez);
+      ey = fmaf(c, k[n + i], ey);
+      ez = fmaf(c, k[2 * n + i], ez);
     }
     e = sqrtf(ex * ex + ey * ey + ez * ez);
     if (!(e <= FLT_MAX)) e = __int_as_float(0x7f800000);
     float* __restrict__ mnew = (par ? p.m0 : p.m1) + o;
-    const float mx = ms[o + i], my = ms[o + g.n + i], mz = ms[o + 2 * g.n + i];
+    const float* __restrict__ mso = ms + o;
+    const float mx = mso[i], my = mso[n + i], mz = mso[2 * n + i];
     const float inv = rsqrtf(mx * mx + my * my + mz * mz);
     mnew[i] = mx * inv;
-    mnew[g.n + i] = my * inv;
-    mnew[2 * g.n + i] = mz * inv;
+    mnew[n + i] = my * inv;
+    mnew[2 * n + i] = mz * inv;
   }
   for (int off = 16; off > 0; off >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, off));
   __shared__ float wmax[32];

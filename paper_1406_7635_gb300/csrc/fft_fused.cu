@@ -29,12 +29,13 @@ namespace {
 using namespace mmfft;
 
 __device__ __forceinline__ float cell_msat_f(const RegionLUT* __restrict__ lut, const uint8_t* __restrict__ mask,
-                                             const uint8_t* __restrict__ region, long long i) {
+                                             const uint8_t* __restrict__ region, int i) {
   return mask[i] ? __ldg(&lut->msat[region[i]]) : 0.0f;
 }
 
-__device__ __forceinline__ long long tidx(const Geom& g, int c, int kx, int z, int y) {
-  return (((long long)c * g.hx + kx) * g.nz + z) * g.ny + y;
+// offset in one instance's spectrum (3 hx nz ny < 2^31 points: nz <= 32)
+__device__ __forceinline__ int tidx(const Geom& g, int c, int kx, int z, int y) {
+  return ((c * g.hx + kx) * g.nz + z) * g.ny + y;
 }
 
 // ----------------------------------------------------------------------------
@@ -61,25 +62,26 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
   load_twiddles<L, NT>(twl, tw);
   for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
   const bool even = (g.nx & 1) == 0;
+  const float* __restrict__ mc = m + c * (int)g.n;   // this component (3 n < 2^31)
   for (int e = threadIdx.x; e < ROWS * L; e += NT) {
     const int r = e / L, n = e % L, y = y0 + r;
     float2 v = make_float2(0.f, 0.f);
     if (y < g.ny) {
-      const long long cell0 = ((long long)z * g.ny + y) * g.nx;
+      const int cell0 = (z * g.ny + y) * g.nx;
       const int x0 = 2 * n, x1 = 2 * n + 1;
       if (ba.msat) {
-        if (x0 < g.nx) v.x = inst_ms * m[c * g.n + cell0 + x0];
-        if (x1 < g.nx) v.y = inst_ms * m[c * g.n + cell0 + x1];
+        if (x0 < g.nx) v.x = inst_ms * mc[cell0 + x0];
+        if (x1 < g.nx) v.y = inst_ms * mc[cell0 + x1];
       } else if (even && x1 < g.nx) {
         // cell0 + x0 is even: aligned pair loads
-        const float2 mv = *reinterpret_cast<const float2*>(m + c * g.n + cell0 + x0);
+        const float2 mv = *reinterpret_cast<const float2*>(mc + cell0 + x0);
         const uchar2 mk = *reinterpret_cast<const uchar2*>(mask + cell0 + x0);
         const uchar2 rg = *reinterpret_cast<const uchar2*>(region + cell0 + x0);
         v.x = mk.x ? __ldg(&lut->msat[rg.x]) * mv.x : 0.f;
         v.y = mk.y ? __ldg(&lut->msat[rg.y]) * mv.y : 0.f;
       } else {
-        if (x0 < g.nx) v.x = cell_msat_f(lut, mask, region, cell0 + x0) * m[c * g.n + cell0 + x0];
-        if (x1 < g.nx) v.y = cell_msat_f(lut, mask, region, cell0 + x1) * m[c * g.n + cell0 + x1];
+        if (x0 < g.nx) v.x = cell_msat_f(lut, mask, region, cell0 + x0) * mc[cell0 + x0];
+        if (x1 < g.nx) v.y = cell_msat_f(lut, mask, region, cell0 + x1) * mc[cell0 + x1];
       }
     }
     s[r * PST + n] = v;
@@ -141,16 +143,17 @@ __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ 
   }
   __syncthreads();
   FftG<L, 1, ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  float* __restrict__ oc = out + c * (int)g.n;
   for (int e = threadIdx.x; e < ROWS * L; e += NT) {
     const int r = e / L, n = e % L, y = y0 + r;
     if (y >= g.ny) continue;
-    const long long cell0 = ((long long)z * g.ny + y) * g.nx;
+    const int cell0 = (z * g.ny + y) * g.nx;
     const float2 v = s[r * PST + n];
     if ((g.nx & 1) == 0 && 2 * n + 1 < g.nx) {
-      *reinterpret_cast<float2*>(out + c * g.n + cell0 + 2 * n) = v;
+      *reinterpret_cast<float2*>(oc + cell0 + 2 * n) = v;
     } else {
-      if (2 * n < g.nx) out[c * g.n + cell0 + 2 * n] = v.x;
-      if (2 * n + 1 < g.nx) out[c * g.n + cell0 + 2 * n + 1] = v.y;
+      if (2 * n < g.nx) oc[cell0 + 2 * n] = v.x;
+      if (2 * n + 1 < g.nx) oc[cell0 + 2 * n + 1] = v.y;
     }
   }
 }
@@ -166,7 +169,7 @@ __device__ __forceinline__ void kernel_mul(float2* s, const float* __restrict__ 
   constexpr int PW = YW * LZ;
   constexpr int PPT = (PW + NTH - 1) / NTH;   // points per thread
   constexpr int CH = PPT < CHMAX ? PPT : CHMAX;
-  const long long per = (long long)g.hky * g.hkz;
+  const int per = g.hky * g.hkz;   // octant: 6 hkx hky hkz < 2^31 floats
 #pragma unroll
   for (int q0 = 0; q0 < PPT; q0 += CH) {
     float kc[CH][6];
@@ -181,7 +184,7 @@ __device__ __forceinline__ void kernel_mul(float2* s, const float* __restrict__ 
       float sy = 1.f, sz = 1.f;
       if (ky > g.py / 2) { iy = g.py - ky; sy = -1.f; }
       if (kz > g.pz / 2) { iz = g.pz - kz; sz = -1.f; }
-      const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
+      const int o = kx * 6 * per + iz * g.hky + iy;
 #pragma unroll
       for (int t = 0; t < 6; ++t) kc[q][t] = __ldg(&kt[t * per + o]);
       sgn[q][0] = sy;
@@ -224,7 +227,7 @@ __device__ __forceinline__ void z_mid(float2* s, const float2* __restrict__ twz,
   constexpr int R0 = LZ / R1;
   constexpr int TOT = R0 * LY;
   constexpr int PER = (TOT + NT - 1) / NT;
-  const long long per = (long long)g.hky * g.hkz;
+  const int per = g.hky * g.hkz;   // octant: 6 hkx hky hkz < 2^31 floats
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int b = threadIdx.x + q * NT;
@@ -241,7 +244,7 @@ __device__ __forceinline__ void z_mid(float2* s, const float2* __restrict__ twz,
       int iz = kz;
       sz[r] = 1.f;
       if (kz > g.pz / 2) { iz = g.pz - kz; sz[r] = -1.f; }
-      const long long o = (long long)kx * 6 * per + (long long)iz * g.hky + iy;
+      const int o = kx * 6 * per + iz * g.hky + iy;
 #pragma unroll
       for (int t = 0; t < 6; ++t) kc[r][t] = __ldg(&kt[t * per + o]);
     }
@@ -527,7 +530,7 @@ void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba
 }
 
 __global__ void k_kt_transpose(Geom g, const float* __restrict__ kt, float* __restrict__ ktf) {
-  const long long per = (long long)g.hky * g.hkz;
+  const int per = g.hky * g.hkz;   // octant: 6 hkx hky hkz < 2^31 floats
   const long long total = 6LL * g.hkx * per;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;

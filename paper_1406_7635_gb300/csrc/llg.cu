@@ -24,46 +24,48 @@ namespace {
 __global__ void k_stage_input(Geom g, Ptrs p, float* __restrict__ ms, const DevState* __restrict__ st,
                               const StageCoef* __restrict__ sc, int s) {
   if (st->done) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
+  const int n = (int)g.n;
   if (i >= g.n) return;
   const int par = st->parity;
   const float* __restrict__ m = par ? p.m1 : p.m0;
-  float acc[3] = {m[i], m[g.n + i], m[2 * g.n + i]};
+  float acc[3] = {m[i], m[n + i], m[2 * n + i]};
   for (int j = 0; j < s; ++j) {
     const float a = sc->ah[s][j];
     if (a == 0.0f) continue;
     const float* __restrict__ k = pick_k(p, k_role(j, par));
     acc[0] = fmaf(a, k[i], acc[0]);
-    acc[1] = fmaf(a, k[g.n + i], acc[1]);
-    acc[2] = fmaf(a, k[2 * g.n + i], acc[2]);
+    acc[1] = fmaf(a, k[n + i], acc[1]);
+    acc[2] = fmaf(a, k[2 * n + i], acc[2]);
   }
   ms[i] = acc[0];
-  ms[g.n + i] = acc[1];
-  ms[2 * g.n + i] = acc[2];
+  ms[n + i] = acc[1];
+  ms[2 * n + i] = acc[2];
 }
 
 __global__ void k_torque(Geom g, Buffers b, Terms T, Ptrs p, const DevState* __restrict__ st, int s, double freq,
                          double phase_over_pi) {
   if (st->done) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
+  const int n = (int)g.n;
   if (i >= g.n) return;
   const int par = st->parity;
   const float* __restrict__ m = s == 0 ? (par ? p.m1 : p.m0) : b.ms;
   float* __restrict__ k = pick_k(p, k_role(s, par));
-  const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+  const int x = i % g.nx, y = (i / g.nx) % g.ny, z = i / (g.nx * g.ny);
   const int r = b.code[i];
   if (r == kVacuum) {
-    k[i] = k[g.n + i] = k[2 * g.n + i] = 0.0f;
+    k[i] = k[n + i] = k[2 * n + i] = 0.0f;
     return;
   }
-  const float3 mi = f3(m[i], m[g.n + i], m[2 * g.n + i]);
+  const float3 mi = f3(m[i], m[n + i], m[2 * n + i]);
   const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->stage_t[s]) : 0.0f;
   FieldParts P;
-  field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[g.n + i], b.bd[2 * g.n + i]), P);
+  field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[n + i], b.bd[2 * n + i]), P);
   const float3 tq = llg_torque(mi, total(P), b.lut->gfac[r], b.lut->alpha[r], st->precession);
   k[i] = tq.x;
-  k[g.n + i] = tq.y;
-  k[2 * g.n + i] = tq.z;
+  k[n + i] = tq.y;
+  k[2 * n + i] = tq.z;
 }
 
 __global__ void k_begin(DevState* st, StageCoef* sc, const double* __restrict__ fixed, int mode, long long nsteps,
@@ -86,7 +88,8 @@ __global__ void k_begin(DevState* st, StageCoef* sc, const double* __restrict__ 
 // controller in the last block
 __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict__ st, StageCoef* __restrict__ sc) {
   if (st->done) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
+  const int n = (int)g.n;
   const int par = st->parity;
   float e = 0.0f;
   if (i < g.n) {
@@ -99,18 +102,18 @@ __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict_
         if (c == 0.0f) continue;
         const float* __restrict__ k = pick_k(p, k_role(j, par));
         ex = fmaf(c, k[i], ex);
-        ey = fmaf(c, k[g.n + i], ey);
-        ez = fmaf(c, k[2 * g.n + i], ez);
+        ey = fmaf(c, k[n + i], ey);
+        ez = fmaf(c, k[2 * n + i], ez);
       }
       e = sqrtf(ex * ex + ey * ey + ez * ez);
       if (!(e <= FLT_MAX)) e = __int_as_float(0x7f800000);
-      const float mx = b.ms[i], my = b.ms[g.n + i], mz = b.ms[2 * g.n + i];
+      const float mx = b.ms[i], my = b.ms[n + i], mz = b.ms[2 * n + i];
       const float inv = rsqrtf(mx * mx + my * my + mz * mz);
       mnew[i] = mx * inv;
-      mnew[g.n + i] = my * inv;
-      mnew[2 * g.n + i] = mz * inv;
+      mnew[n + i] = my * inv;
+      mnew[2 * n + i] = mz * inv;
     } else {
-      mnew[i] = mnew[g.n + i] = mnew[2 * g.n + i] = 0.0f;
+      mnew[i] = mnew[n + i] = mnew[2 * n + i] = 0.0f;
     }
   }
   // block max (non-negative floats order like their bit patterns)
@@ -140,19 +143,20 @@ __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict_
 // atomicMax; the host zeroes them first).
 __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict__ m, const DevState* __restrict__ st,
                             int mode, double freq, double phase_over_pi) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
+  const int n = (int)g.n;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   float tmax = 0.0f;
   if (i < g.n) {
-    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+    const int x = i % g.nx, y = (i / g.nx) % g.ny, z = i / (g.nx * g.ny);
     const int r = b.code[i];
     const bool mag = r != kVacuum;
     float3 out = f3(0, 0, 0);
     if (mag) {
-      const float3 mi = f3(m[i], m[g.n + i], m[2 * g.n + i]);
+      const float3 mi = f3(m[i], m[n + i], m[2 * n + i]);
       const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->t) : 0.0f;
       FieldParts P;
-      field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[g.n + i], b.bd[2 * g.n + i]), P);
+      field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[n + i], b.bd[2 * n + i]), P);
       const float3 B = total(P);
       if (mode == 0) out = B;
       else if (mode == 1) out = llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession);
@@ -175,8 +179,8 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
     }
     if (mode < 2) {
       b.out[i] = out.x;
-      b.out[g.n + i] = out.y;
-      b.out[2 * g.n + i] = out.z;
+      b.out[n + i] = out.y;
+      b.out[2 * n + i] = out.z;
     }
   }
   if (mode == 4) {
@@ -201,27 +205,28 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
 
 __global__ void k_normalize(Geom g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ region,
                             const RegionLUT* __restrict__ lut, float* __restrict__ m) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
+  const int n = (int)g.n;
   if (i >= g.n) return;
   const bool mag = is_magnetic(mask, region, lut, i);
-  const float x = m[i], y = m[g.n + i], z = m[2 * g.n + i];
+  const float x = m[i], y = m[n + i], z = m[2 * n + i];
   const float n2 = x * x + y * y + z * z;
   const float inv = (mag && n2 > 0.0f) ? rsqrtf(n2) : 0.0f;
   m[i] = x * inv;
-  m[g.n + i] = y * inv;
-  m[2 * g.n + i] = z * inv;
+  m[n + i] = y * inv;
+  m[2 * n + i] = z * inv;
 }
 
 __global__ void k_codes(Geom g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ region,
                         const RegionLUT* __restrict__ lut, int* __restrict__ code) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28
   if (i >= g.n) return;
   code[i] = is_magnetic(mask, region, lut, i) ? (int)region[i] : kVacuum;
 }
 
 __global__ void k_copy_cur(Geom g, const float* __restrict__ m0, const float* __restrict__ m1,
                            const DevState* __restrict__ st, float* __restrict__ dst) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // 3 n < 2^31
   if (i >= 3 * g.n) return;
   dst[i] = st->parity ? m1[i] : m0[i];
 }

@@ -67,7 +67,7 @@ __device__ __forceinline__ float* pick_k(const Ptrs& p, int j) {
 }
 
 __device__ __forceinline__ bool is_magnetic(const uint8_t* __restrict__ mask, const uint8_t* __restrict__ region,
-                                            const RegionLUT* __restrict__ lut, long long i) {
+                                            const RegionLUT* __restrict__ lut, int i) {
   return mask[i] != 0 && __ldg(&lut->msat[region[i]]) > 0.0f;
 }
 
@@ -107,7 +107,7 @@ __device__ __forceinline__ void field_local(const RegionLUT* __restrict__ lut, c
 // the grid is replaced by the cell itself (m_j - m_i = 0) and a vacuum
 // neighbour has a zero coupling, so the loads carry no branches.
 __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const Terms& T, const float* __restrict__ m,
-                                         long long i, int x, int y, int z, int ci, float3 mi, float sinft,
+                                         int i, int x, int y, int z, int ci, float3 mi, float sinft,
                                          float3 bdemag, FieldParts& P) {
   const RegionLUT* __restrict__ lut = b.lut;
   const int r = ci & (kRegions - 1);
@@ -115,18 +115,18 @@ __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const 
   float3 ex = f3(0, 0, 0);
   if (T.exch) {
     const float* __restrict__ xl = b.xlut + r * kXStride;
-    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-    const long long js[6] = {x > 0 ? i - 1 : i,          x < g.nx - 1 ? i + 1 : i,
+    const int sy = g.nx, sz = g.nx * g.ny, n = (int)g.n;
+    const int js[6] = {x > 0 ? i - 1 : i,          x < g.nx - 1 ? i + 1 : i,
                              y > 0 ? i - sy : i,         y < g.ny - 1 ? i + sy : i,
                              z > 0 ? i - sz : i,         z < g.nz - 1 ? i + sz : i};
     const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-      const long long j = js[d];
+      const int j = js[d];
       const float c = __ldg(&xl[b.code[j]]) * id2[d];
       ex.x += c * (m[j] - mi.x);
-      ex.y += c * (m[g.n + j] - mi.y);
-      ex.z += c * (m[2 * g.n + j] - mi.z);
+      ex.y += c * (m[n + j] - mi.y);
+      ex.z += c * (m[2 * n + j] - mi.z);
     }
   }
   P.exch = ex;
