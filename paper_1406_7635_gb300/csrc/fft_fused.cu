@@ -286,24 +286,25 @@ __device__ __forceinline__ void z_mid(float2* s, const float2* __restrict__ twz,
   }
 }
 
-// Second (last) inverse z pass of one component after z_mid: radix R0,
-// butterfly j2 < R1 reads element r2 at the transposed position r2 + R0 j2
-// and writes the natural order j2 + R1 r2.  Ends with __syncthreads().
-template <int LY, int LZ, int NT, int RP>
+// Second (last) inverse z pass after z_mid, for NC consecutive components
+// (component stride CS): radix R0, butterfly j2 < R1 reads element r2 at the
+// transposed position r2 + R0 j2 and writes the natural order j2 + R1 r2.
+// Ends with __syncthreads().
+template <int LY, int LZ, int NT, int RP, int CS, int NC>
 __device__ __forceinline__ void z_inv_tail(float2* sc, const float2* __restrict__ twz) {
   constexpr int R1 = zmid_radix(LZ);
   constexpr int R0 = LZ / R1;
   if constexpr (R0 > 1) {
-    constexpr int TOT = R1 * LY;
+    constexpr int TOT = R1 * LY * NC;
     constexpr int PER = (TOT + NT - 1) / NT;
     float2 v[PER][R0];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int b = threadIdx.x + q * NT;
       if (TOT % NT == 0 || b < TOT) {
-        const int p = b % LY, j2 = b / LY;
+        const int p = b % LY, cc = (b / LY) % NC, j2 = b / (LY * NC);
 #pragma unroll
-        for (int r = 0; r < R0; ++r) v[q][r] = sc[(r + R0 * j2) * RP + p];
+        for (int r = 0; r < R0; ++r) v[q][r] = sc[cc * CS + (r + R0 * j2) * RP + p];
       }
     }
     __syncthreads();
@@ -311,12 +312,12 @@ __device__ __forceinline__ void z_inv_tail(float2* sc, const float2* __restrict_
     for (int q = 0; q < PER; ++q) {
       const int b = threadIdx.x + q * NT;
       if (TOT % NT == 0 || b < TOT) {
-        const int p = b % LY, j2 = b / LY;
+        const int p = b % LY, cc = (b / LY) % NC, j2 = b / (LY * NC);
 #pragma unroll
         for (int r = 1; r < R0; ++r) v[q][r] = cmul(v[q][r], cconj(twz[(r * j2) & (LZ - 1)]));
         Dft<R0, 1>::run(v[q]);
 #pragma unroll
-        for (int r = 0; r < R0; ++r) sc[(j2 + R1 * r) * RP + p] = v[q][r];
+        for (int r = 0; r < R0; ++r) sc[cc * CS + (j2 + R1 * r) * RP + p] = v[q][r];
       }
     }
   }
@@ -380,20 +381,23 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   //    (y ry / py + z rz / pz)) is applied as the first pass loads its inputs
   if constexpr (LZ > 1) {
     constexpr int R0 = LZ / zmid_radix(LZ);
-    for (int c = 0; c < 3; ++c) {
-      FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
-      if constexpr (R0 > 1)
-        stockham_pass<LZ, R0, 1, -1, LY, NT, LY, CS, RP, LZ>(s + c * CS, twz, rz ? rtz : nullptr);
+    // (the three components' rows are one array of 3 LZ rows at pitch RP:
+    // components 0 and 1 are transformed together, then component 2)
+    FftG<LY, -1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy, ry ? rty : nullptr);
+    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy, ry ? rty : nullptr);
+    if constexpr (R0 > 1) {
+      stockham_pass<LZ, R0, 1, -1, 2 * LY, NT, LY, CS, RP, LZ>(s, twz, rz ? rtz : nullptr);
+      stockham_pass<LZ, R0, 1, -1, LY, NT, LY, CS, RP, LZ>(s + 2 * CS, twz, rz ? rtz : nullptr);
     }
     // 3. last forward z pass, kernel multiply at (kx, ky = CLY j + ry,
     //    kz = CLZ l + rz), first inverse z pass, all in registers
     z_mid<LY, LZ, NT, RP, CS>(s, twz, rtz, kt, g, kx, ry, rz);
     __syncthreads();
     // 4. rest of the inverse transforms
-    for (int c = 0; c < 3; ++c) {
-      z_inv_tail<LY, LZ, NT, RP>(s + c * CS, twz);
-      FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
-    }
+    z_inv_tail<LY, LZ, NT, RP, CS, 2>(s, twz);
+    z_inv_tail<LY, LZ, NT, RP, CS, 1>(s + 2 * CS, twz);
+    FftG<LY, 1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy);
+    FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy);
   } else {
     for (int c = 0; c < 3; ++c) FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
     kernel_mul<LY, LZ, RP, CS, LY, NT, 2>(s, kt, g, kx, ry, rz, 0, threadIdx.x);
