@@ -4,6 +4,7 @@ E_demag = -1/2 sum M.B_demag V           (energy density of the demag term)
 E_exch  = -1/2 sum M.B_exch V            (Eq. eqEdensExch)
 E_anis  = -1/2 sum M.B_anis(Ku1) V - 1/4 sum M.B_anis(Ku2) V   (Eq. EaniUM)
 E_Z     = -sum M.B_ext V                 (Zeeman energy density -M.B)
+E_DM    = -1/2 sum M.B_DM V              (Eq. eqEdensDMI)
 <m>     = average of m over the magnetic cells.
 """
 import numpy as np
@@ -26,8 +27,9 @@ def energies(p, m, t, field=None):
         "exch": -0.5 * dot(terms["exch"]),
         "anis": -0.5 * dot(terms["anis1"]) - 0.25 * dot(terms["anis2"]),
         "zeeman": -dot(terms["zeeman"]),
+        "dmi": -0.5 * dot(terms["dmi"]),
     }
-    e["total"] = e["demag"] + e["exch"] + e["anis"] + e["zeeman"]
+    e["total"] = e["demag"] + e["exch"] + e["anis"] + e["zeeman"] + e["dmi"]
     nmag = int(mag.sum())
     e["m_avg"] = [float(m[c][mag].sum()) / nmag if nmag else 0.0 for c in range(3)]
     return e

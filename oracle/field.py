@@ -1,8 +1,9 @@
 """Effective field and Landau-Lifshitz torque (Sec. III), float64.
 
-B_eff = B_ext + B_demag + B_exch + B_anis (the terms this path needs; DMI,
-thermal and spin-transfer terms are outside it).  Non-magnetic cells (mask 0
-or Msat 0) carry m = 0, B_eff = 0 and zero torque.
+B_eff = B_ext + B_demag + B_exch + B_anis + B_DM (the interfacial DMI term
+and its boundary conditions are in dmi.py; thermal and spin-transfer terms
+are outside this path).  Non-magnetic cells (mask 0 or Msat 0) carry m = 0,
+B_eff = 0 and zero torque.
 """
 import numpy as np
 
@@ -89,7 +90,14 @@ def effective_field(p, m, t, demag_method="fft", spectrum=None):
             terms["demag"] = demag_fft(M, p.dx, p.dy, p.dz, spectrum=spectrum)
     else:
         terms["demag"] = zero
-    terms["exch"] = exchange_field(p, m) if p.exch else zero
+    has_dmi = bool(np.any(p.dind[np.unique(p.region)] != 0))
+    if has_dmi:
+        from .dmi import dmi_field, exchange_field_bc
+        terms["exch"] = exchange_field_bc(p, m) if p.exch else zero
+        terms["dmi"] = dmi_field(p, m)
+    else:
+        terms["exch"] = exchange_field(p, m) if p.exch else zero
+        terms["dmi"] = zero
     if p.anis:
         a1, a2 = anisotropy_field_parts(p, m)
         terms["anis1"], terms["anis2"] = a1, a2
@@ -97,7 +105,7 @@ def effective_field(p, m, t, demag_method="fft", spectrum=None):
         terms["anis1"] = terms["anis2"] = zero
     terms["zeeman"] = zeeman_field(p, t) if p.zeeman else zero
     total = (terms["demag"] + terms["exch"] + terms["anis1"] + terms["anis2"]
-             + terms["zeeman"])
+             + terms["zeeman"] + terms["dmi"])
     terms["total"] = total * mag[None]
     return terms
 

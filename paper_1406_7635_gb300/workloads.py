@@ -45,6 +45,7 @@ class Problem:
     gamma: np.ndarray = field(default_factory=lambda: np.full(256, GAMMA_LL))
     ku1: np.ndarray = field(default_factory=lambda: _zeros256())
     ku2: np.ndarray = field(default_factory=lambda: _zeros256())
+    dind: np.ndarray = field(default_factory=lambda: _zeros256())   # interfacial DMI constant D (J/m^2)
     anis_u: np.ndarray = field(default_factory=lambda: np.tile([1.0, 0.0, 0.0], (256, 1)))
     exch_scale: np.ndarray = field(default_factory=lambda: np.ones((256, 256)))
     b0: np.ndarray = field(default_factory=lambda: _zeros256(3))
