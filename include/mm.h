@@ -53,11 +53,18 @@ typedef struct {
   double gamma_ll;  /* gyromagnetic ratio (rad/(T s)); 1.7595e11 by default    */
   double ku1, ku2;  /* uniaxial anisotropy constants (J/m^3), Sec. III.E      */
   double anis_u[3]; /* anisotropy axis (normalised by the library)            */
+  double dind;      /* interfacial DMI constant D (J/m^2), Sec. III "Dzyaloshinskii-
+                       Moriya interaction": B_DM = (2D/Msat)(dmz/dx, dmz/dy,
+                       -dmx/dx - dmy/dy) by central differences; at a missing
+                       neighbour (grid edge or vacuum) the Rohart boundary
+                       conditions give a ghost value, used by exchange too.
+                       D and Aex of the cell's own region; 0 = no DMI        */
 } mm_material;
 
 typedef struct {
-  double total, demag, exch, anis, zeeman; /* J */
+  double total, demag, exch, anis, zeeman; /* J (total includes dmi)      */
   double m_avg[3];                         /* average m over magnetic cells */
+  double dmi;                              /* J, -1/2 M.B_DM V summed       */
 } mm_energies;
 
 typedef struct {

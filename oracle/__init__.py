@@ -19,7 +19,12 @@ paper ("The design and verification of Mumax3", Vansteenkiste et al.) by eye:
 * ``field``   -- exchange (Eqs. for B_exch incl. the inter-region harmonic
   mean), uniaxial anisotropy, Zeeman, effective field, Landau-Lifshitz torque
   (Eq. eqLLG).
+* ``dmi``     -- interfacial Dzyaloshinskii-Moriya field and its boundary
+  conditions (Sec. III).
 * ``rk45``    -- Dormand-Prince RK45 with the adaptive step control of Sec. IV.
+* ``relax``   -- Bogacki-Shampine RK23 and relax() (Sec. IV).
+* ``fno``     -- the Fourier-neural-operator surrogate of the demag field
+  (forward and backward; the paper has none).
 * ``energy``  -- energies from the effective field (Eqs. for E_demag, E_exch,
   E_anis).
 

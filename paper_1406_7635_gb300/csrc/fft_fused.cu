@@ -399,10 +399,11 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
     FftG<LY, 1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy);
     FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy);
   } else {
-    for (int c = 0; c < 3; ++c) FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy, ry ? rty : nullptr);
+    // 2-D: the three components are three rows at pitch RP, transformed together
+    FftG<LY, -1, 3, NT, 1, RP, 1, LY>::run(s, twy, ry ? rty : nullptr);
     kernel_mul<LY, LZ, RP, CS, LY, NT, 2>(s, kt, g, kx, ry, rz, 0, threadIdx.x);
     __syncthreads();
-    for (int c = 0; c < 3; ++c) FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + c * CS, twy);
+    FftG<LY, 1, 3, NT, 1, RP, 1, LY>::run(s, twy);
   }
   // 5. sum the class contributions across the cluster, each multiplied by
   //    the conjugate of its class twiddle; each block stores one contiguous
@@ -503,7 +504,8 @@ int xrow_options(int* out) {
 
 template <int LY, int LZ>
 struct YzCfg {
-  static constexpr int B0 = LY * LZ / 8;    // radix-8 butterflies per component
+  // radix-8 butterflies per component (2-D: of all three components)
+  static constexpr int B0 = LZ == 1 ? 3 * LY / 8 : LY * LZ / 8;
   static constexpr int NT = B0 < 64 ? 64 : (B0 > 512 ? 512 : B0);
   static constexpr size_t SMEM = sizeof(float2) * (3 * LZ * (LY + 1) + 2 * (LY + LZ));
 };

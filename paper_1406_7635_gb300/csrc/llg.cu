@@ -137,7 +137,7 @@ __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict_
 }
 
 // Getters: mode 0 writes B_eff, mode 1 the torque, mode 2 accumulates energies
-// (float64) into acc[0..7] = {demag, exch, anis, zeeman, mx, my, mz, ncells}
+// (float64) into acc[0..8] = {demag, exch, anis, zeeman, mx, my, mz, ncells, dmi}
 // (M.B sums; the host multiplies by the cell volume), mode 4 the maximum of
 // |torque| over the magnetic cells into the first 4 bytes of acc (float bits,
 // atomicMax; the host zeroes them first).
@@ -145,7 +145,7 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
                             int mode, double freq, double phase_over_pi) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
   const int n = (int)g.n;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   float tmax = 0.0f;
   if (i < g.n) {
     const int x = i % g.nx, y = (i / g.nx) % g.ny, z = i / (g.nx * g.ny);
@@ -175,6 +175,7 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
         acc[5] = mi.y;
         acc[6] = mi.z;
         acc[7] = 1.0;
+        acc[8] = -0.5 * dot(P.dmi);
       }
     }
     if (mode < 2) {
@@ -188,14 +189,14 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(b.acc), __float_as_uint(tmax));
   }
   if (mode == 2) {
-    __shared__ double red[8][32];
-    for (int c = 0; c < 8; ++c) {
+    __shared__ double red[9][32];
+    for (int c = 0; c < 9; ++c) {
       double v = acc[c];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < 9) {
       double v = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
       atomicAdd(&b.acc[threadIdx.x], v);

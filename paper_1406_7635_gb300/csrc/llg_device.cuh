@@ -75,7 +75,7 @@ __device__ __forceinline__ bool is_magnetic(const uint8_t* __restrict__ mask, co
 // effective field at one cell
 // ----------------------------------------------------------------------------
 struct FieldParts {
-  float3 demag, exch, anis1, anis2, zee;
+  float3 demag, exch, anis1, anis2, zee, dmi;
 };
 
 __device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
@@ -102,6 +102,30 @@ __device__ __forceinline__ void field_local(const RegionLUT* __restrict__ lut, c
   }
 }
 
+// Ghost value of a missing neighbour in direction d (0 x-, 1 x+, 2 y-, 3 y+,
+// 4 z-, 5 z+) under the boundary conditions of the interfacial DMI (Sec. III,
+// "Dzyaloshinskii-Moriya interaction"): m + n Delta dm/di with the outward
+// normal n and dm/dx = (-c mz, 0, c mx), dm/dy = (0, -c mz, c my), dm/dz = 0,
+// c = D / (2 Aex).  With c = 0 it is m itself (the plain Neumann edge).
+__device__ __forceinline__ float3 dmi_ghost(float3 m, int d, float c, float dx, float dy) {
+  switch (d) {
+    case 0: return f3(m.x + dx * c * m.z, m.y, m.z - dx * c * m.x);
+    case 1: return f3(m.x - dx * c * m.z, m.y, m.z + dx * c * m.x);
+    case 2: return f3(m.x, m.y + dy * c * m.z, m.z - dy * c * m.y);
+    case 3: return f3(m.x, m.y - dy * c * m.z, m.z + dy * c * m.y);
+    default: return m;
+  }
+}
+
+// B_DM = (2D/Msat)(dmz/dx, dmz/dy, -dmx/dx - dmy/dy), central differences
+// over the x-, x+, y-, y+ neighbour values (present or ghost)
+__device__ __forceinline__ float3 dmi_field(float pref, float3 xm, float3 xp, float3 ym, float3 yp, float dx,
+                                            float dy) {
+  const float hx = 0.5f / dx, hy = 0.5f / dy;
+  return f3(pref * (xp.z - xm.z) * hx, pref * (yp.z - ym.z) * hy,
+            -pref * ((xp.x - xm.x) * hx + (yp.y - ym.y) * hy));
+}
+
 // Effective field at cell i of code ci (a magnetic cell: ci < kVacuum).
 // Exchange: the six neighbours are read unconditionally; a neighbour outside
 // the grid is replaced by the cell itself (m_j - m_i = 0) and a vacuum
@@ -112,21 +136,42 @@ __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const 
   const RegionLUT* __restrict__ lut = b.lut;
   const int r = ci & (kRegions - 1);
   P.demag = T.demag ? bdemag : f3(0, 0, 0);
+  P.dmi = f3(0, 0, 0);
   float3 ex = f3(0, 0, 0);
-  if (T.exch) {
+  if (T.exch || T.dmi) {
     const float* __restrict__ xl = b.xlut + r * kXStride;
     const int sy = g.nx, sz = g.nx * g.ny, n = (int)g.n;
     const int js[6] = {x > 0 ? i - 1 : i,          x < g.nx - 1 ? i + 1 : i,
                              y > 0 ? i - sy : i,         y < g.ny - 1 ? i + sy : i,
                              z > 0 ? i - sz : i,         z < g.nz - 1 ? i + sz : i};
     const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
+    if (!T.dmi) {
 #pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      const int j = js[d];
-      const float c = __ldg(&xl[b.code[j]]) * id2[d];
-      ex.x += c * (m[j] - mi.x);
-      ex.y += c * (m[n + j] - mi.y);
-      ex.z += c * (m[2 * n + j] - mi.z);
+      for (int d = 0; d < 6; ++d) {
+        const int j = js[d];
+        const float c = __ldg(&xl[b.code[j]]) * id2[d];
+        ex.x += c * (m[j] - mi.x);
+        ex.y += c * (m[n + j] - mi.y);
+        ex.z += c * (m[2 * n + j] - mi.z);
+      }
+    } else {
+      // a missing neighbour (grid edge or vacuum) is the ghost value, coupled
+      // with the cell's own 2 Aex/Msat; the in-plane values feed B_DM
+      const float cbc = __ldg(&lut->dbc[r]);
+      float3 v[4];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int j = js[d];
+        const int cj = b.code[j];
+        const bool present = j != i && cj != kVacuum;
+        const float3 mj = present ? f3(m[j], m[n + j], m[2 * n + j]) : dmi_ghost(mi, d, cbc, g.cdx, g.cdy);
+        const float c = T.exch ? __ldg(&xl[present ? cj : r]) * id2[d] : 0.0f;
+        ex.x += c * (mj.x - mi.x);
+        ex.y += c * (mj.y - mi.y);
+        ex.z += c * (mj.z - mi.z);
+        if (d < 4) v[d] = mj;
+      }
+      P.dmi = dmi_field(__ldg(&lut->dmi[r]), v[0], v[1], v[2], v[3], g.cdx, g.cdy);
     }
   }
   P.exch = ex;
@@ -134,10 +179,11 @@ __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const 
 }
 
 __device__ __forceinline__ float3 total(const FieldParts& P) {
-  return f3(P.demag.x + P.exch.x + P.anis1.x + P.anis2.x + P.zee.x,
-            P.demag.y + P.exch.y + P.anis1.y + P.anis2.y + P.zee.y,
-            P.demag.z + P.exch.z + P.anis1.z + P.anis2.z + P.zee.z);
+  return f3(P.demag.x + P.exch.x + P.anis1.x + P.anis2.x + P.zee.x + P.dmi.x,
+            P.demag.y + P.exch.y + P.anis1.y + P.anis2.y + P.zee.y + P.dmi.y,
+            P.demag.z + P.exch.z + P.anis1.z + P.anis2.z + P.zee.z + P.dmi.z);
 }
+
 
 __device__ __forceinline__ float3 llg_torque(float3 m, float3 B, float gfac, float alpha, int precession) {
   const float3 mxB = f3(m.y * B.z - m.z * B.y, m.z * B.x - m.x * B.z, m.x * B.y - m.y * B.x);

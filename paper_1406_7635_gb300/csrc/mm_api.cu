@@ -65,7 +65,7 @@ struct mm_ctx {
   std::vector<double> S;        // [256][256]
   double b0[kRegions][3]{}, b1[kRegions][3]{};
   double freq = 0, phase = 0;
-  Terms T{1, 1, 1, 1};
+  Terms T{1, 1, 1, 1, 0};
   int method = 0;                // host copy of DevState::method
   bool lut_dirty = true;
   bool m_set = false;
@@ -109,6 +109,7 @@ int flush_luts(mm_ctx* c) {
   RegionLUT L{};
   std::vector<float> X((size_t)kRegions * kXStride, 0.0f);
   double a[kRegions];
+  int dmi = 0;
   for (int r = 0; r < kRegions; ++r) {
     const mm_material& m = c->mat[r];
     L.msat[r] = (float)m.msat;
@@ -124,6 +125,9 @@ int flush_luts(mm_ctx* c) {
       L.b1[k][r] = (float)c->b1[r][k];
     }
     a[r] = m.msat > 0 ? m.aex / m.msat : 0.0;
+    L.dmi[r] = m.msat > 0 ? (float)(2.0 * m.dind / m.msat) : 0.0f;
+    L.dbc[r] = m.aex > 0 ? (float)(m.dind / (2.0 * m.aex)) : 0.0f;
+    if (m.msat > 0 && m.dind != 0.0) dmi = 1;
   }
   // 2 S(r1, r2) * harmonic mean of Aex/Msat (inter-region exchange)
   for (int r1 = 0; r1 < kRegions; ++r1)
@@ -138,6 +142,11 @@ int flush_luts(mm_ctx* c) {
   MM_CUDA(cudaGetLastError());
   MM_CUDA(cudaStreamSynchronize(c->stream));
   c->lut_dirty = false;
+  if (dmi != c->T.dmi) {   // the DMI term and its boundary ghosts switch on or off
+    c->T.dmi = dmi;
+    c->graph_valid = false;
+    c->k1_valid = false;
+  }
   return MM_OK;
 }
 
@@ -275,7 +284,7 @@ int eval_field(mm_ctx* c, int mode) {
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
   if (c->T.demag || mode == 3) launch_demag(c->g, nb, c->b.ms, c->stream);
   if (mode == 3) return MM_OK;
-  if (mode == 2 || mode == 4) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 8 * sizeof(double), c->stream));
+  if (mode == 2 || mode == 4) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 9 * sizeof(double), c->stream));
   Terms T = c->T;
   launch_field_out_t(c->g, c->b, T, c->b.ms, mode, c->freq, c->phase, c->stream);
   MM_CUDA(cudaGetLastError());
@@ -296,6 +305,8 @@ Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz) {
   g.nz = nz;
   g.n = (long long)nx * ny * nz;
   g.idx2 = (float)(1.0 / (dx * dx));
+  g.cdx = (float)dx;
+  g.cdy = (float)dy;
   g.idy2 = (float)(1.0 / (dy * dy));
   g.idz2 = (float)(1.0 / (dz * dz));
   g.px = nx == 1 ? 1 : next_pow2(2 * nx - 1);
@@ -376,7 +387,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   alloc((void**)&b.code, (size_t)g.n * sizeof(int));
   alloc((void**)&b.st, devstate_bytes());
   alloc((void**)&b.hist, (size_t)kHistCap * sizeof(double));
-  alloc((void**)&b.acc, 8 * sizeof(double));
+  alloc((void**)&b.acc, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->st_host, sizeof(DevState));
   if (e != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, cudaGetErrorString(e)));
@@ -469,8 +480,8 @@ int mm_set_regions(mm_ctx* c, const uint8_t* region) {
 int mm_set_region_material(mm_ctx* c, int region, const mm_material* mat) {
   if (!c || !mat) return fail(MM_ERR_ARG, "NULL argument");
   if (region < 0 || region >= kRegions) return fail(MM_ERR_ARG, "region must be 0..255");
-  if (mat->msat < 0 || mat->aex < 0 || mat->alpha < 0 || !std::isfinite(mat->gamma_ll))
-    return fail(MM_ERR_ARG, "msat, aex, alpha must be >= 0");
+  if (mat->msat < 0 || mat->aex < 0 || mat->alpha < 0 || !std::isfinite(mat->gamma_ll) || !std::isfinite(mat->dind))
+    return fail(MM_ERR_ARG, "msat, aex, alpha must be >= 0 and gamma_ll, dind finite");
   c->mat[region] = *mat;
   c->lut_dirty = true;
   invalidate(c);
@@ -512,7 +523,7 @@ int mm_set_bext_timefn(mm_ctx* c, double freq, double phase) {
 
 int mm_enable_terms(mm_ctx* c, int demag, int exch, int anis, int zeeman, int precession) {
   if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
-  c->T = Terms{demag != 0, exch != 0, anis != 0, zeeman != 0};
+  c->T = Terms{demag != 0, exch != 0, anis != 0, zeeman != 0, c->T.dmi};
   int rc = read_state(c);
   if (rc) return rc;
   c->st_host->precession = precession != 0;
@@ -707,7 +718,7 @@ int mm_get_energies(mm_ctx* c, mm_energies* out) {
   if (!c || !out) return fail(MM_ERR_ARG, "NULL argument");
   int rc = eval_field(c, 2);
   if (rc) return rc;
-  double acc[8];
+  double acc[9];
   MM_CUDA(cudaMemcpyAsync(acc, c->b.acc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
   MM_CUDA(cudaStreamSynchronize(c->stream));
   const double V = c->dx * c->dy * c->dz;
@@ -715,7 +726,8 @@ int mm_get_energies(mm_ctx* c, mm_energies* out) {
   out->exch = acc[1] * V;
   out->anis = acc[2] * V;
   out->zeeman = acc[3] * V;
-  out->total = out->demag + out->exch + out->anis + out->zeeman;
+  out->dmi = acc[8] * V;
+  out->total = out->demag + out->exch + out->anis + out->zeeman + out->dmi;
   for (int k = 0; k < 3; ++k) out->m_avg[k] = acc[7] > 0 ? acc[4 + k] / acc[7] : 0.0;
   return MM_OK;
 }

@@ -26,6 +26,8 @@ struct RegionLUT {
   float u[3][kRegions];   // anisotropy axis
   float b0[3][kRegions];  // B_ext = b0 + b1 sin(2 pi f t + phase)
   float b1[3][kRegions];
+  float dmi[kRegions];    // 2 D / Msat                (interfacial DMI field)
+  float dbc[kRegions];    // D / (2 Aex)              (boundary derivative; 0 if Aex = 0)
 };
 
 // Grid and padded-FFT geometry.
@@ -44,6 +46,7 @@ struct Geom {
   // cluster of cly*clz blocks per kx plane, each transforming ly x lz points
   int fused, cly, clz, ly, lz;
   int xrows;              // x-row kernels: rows per block (0 = default rule)
+  float cdx, cdy;         // cell sizes along x and y (DMI ghost values)
 };
 
 // Integrator state on the device (one per context).  Every kernel of a step
@@ -91,7 +94,8 @@ struct Buffers {
   float* out;         // field/torque output for getters
 };
 
-struct Terms { int demag, exch, anis, zeeman; };
+// enabled field terms; dmi is set by the library when a region has D != 0
+struct Terms { int demag, exch, anis, zeeman, dmi; };
 
 Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz);
 

@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
                            sf[2 * (2 * ROWS + r) * PST + x])
                       : f3(0, 0, 0);
     float3 ex = f3(0, 0, 0);
-    if (T.exch) {
+    P.dmi = f3(0, 0, 0);
+    if (T.exch || T.dmi) {
       // same neighbour order and arithmetic as field_at
       const float* __restrict__ xl = b.xlut + ci * kXStride;
       const int nb[6] = {x > 0 ? C - 1 : C,
@@ -306,13 +307,33 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
                          z > 0 ? (ROWS + 2 + r) * L + x : C,
                          z < g.nz - 1 ? (2 * ROWS + 2 + r) * L + x : C};
       const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
+      if (!T.dmi) {
 #pragma unroll
-      for (int d = 0; d < 6; ++d) {
-        const int j = nb[d];
-        const float c = __ldg(&xl[scode[j]]) * id2[d];
-        ex.x += c * (sten[j] - mi.x);
-        ex.y += c * (sten[NR * L + j] - mi.y);
-        ex.z += c * (sten[2 * NR * L + j] - mi.z);
+        for (int d = 0; d < 6; ++d) {
+          const int j = nb[d];
+          const float c = __ldg(&xl[scode[j]]) * id2[d];
+          ex.x += c * (sten[j] - mi.x);
+          ex.y += c * (sten[NR * L + j] - mi.y);
+          ex.z += c * (sten[2 * NR * L + j] - mi.z);
+        }
+      } else {
+        // missing neighbours (grid edge or vacuum) are the DMI ghost values
+        const float cbc = __ldg(&lut->dbc[ci]);
+        float3 v[4];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          const int j = nb[d];
+          const int cj = scode[j];
+          const bool present = j != C && cj != kVacuum;
+          const float3 mj = present ? f3(sten[j], sten[NR * L + j], sten[2 * NR * L + j])
+                                    : dmi_ghost(mi, d, cbc, g.cdx, g.cdy);
+          const float c = T.exch ? __ldg(&xl[present ? cj : ci]) * id2[d] : 0.0f;
+          ex.x += c * (mj.x - mi.x);
+          ex.y += c * (mj.y - mi.y);
+          ex.z += c * (mj.z - mi.z);
+          if (d < 4) v[d] = mj;
+        }
+        P.dmi = dmi_field(__ldg(&lut->dmi[ci]), v[0], v[1], v[2], v[3], g.cdx, g.cdy);
       }
     }
     P.exch = ex;

@@ -33,12 +33,12 @@ class MMError(RuntimeError):
 
 class mm_material(C.Structure):
     _fields_ = [("msat", C.c_double), ("aex", C.c_double), ("alpha", C.c_double), ("gamma_ll", C.c_double),
-                ("ku1", C.c_double), ("ku2", C.c_double), ("anis_u", C.c_double * 3)]
+                ("ku1", C.c_double), ("ku2", C.c_double), ("anis_u", C.c_double * 3), ("dind", C.c_double)]
 
 
 class mm_energies(C.Structure):
     _fields_ = [("total", C.c_double), ("demag", C.c_double), ("exch", C.c_double), ("anis", C.c_double),
-                ("zeeman", C.c_double), ("m_avg", C.c_double * 3)]
+                ("zeeman", C.c_double), ("m_avg", C.c_double * 3), ("dmi", C.c_double)]
 
 
 class mm_stats(C.Structure):
@@ -191,8 +191,9 @@ class Context:
         a = None if region is None else np.ascontiguousarray(region, dtype=np.uint8).reshape(self.shape)
         _check(mm_set_regions(self.h, None if a is None else _ptr(a)))
 
-    def set_material(self, region, msat, aex, alpha, gamma_ll=1.7595e11, ku1=0.0, ku2=0.0, anis_u=(1.0, 0.0, 0.0)):
-        m = mm_material(msat, aex, alpha, gamma_ll, ku1, ku2, (C.c_double * 3)(*anis_u))
+    def set_material(self, region, msat, aex, alpha, gamma_ll=1.7595e11, ku1=0.0, ku2=0.0, anis_u=(1.0, 0.0, 0.0),
+                     dind=0.0):
+        m = mm_material(msat, aex, alpha, gamma_ll, ku1, ku2, (C.c_double * 3)(*anis_u), dind)
         _check(mm_set_region_material(self.h, region, C.byref(m)))
 
     def set_exchange_scale(self, r1, r2, s):
@@ -266,7 +267,7 @@ class Context:
         e = mm_energies()
         _check(mm_get_energies(self.h, C.byref(e)))
         return {"total": e.total, "demag": e.demag, "exch": e.exch, "anis": e.anis, "zeeman": e.zeeman,
-                "m_avg": list(e.m_avg)}
+                "dmi": e.dmi, "m_avg": list(e.m_avg)}
 
     def get_max_torque(self):
         v = C.c_double()
@@ -342,7 +343,8 @@ class Context:
         used = np.unique(p.region) if regions_used is None else regions_used
         for r in used:
             r = int(r)
-            ctx.set_material(r, p.msat[r], p.aex[r], p.alpha[r], p.gamma[r], p.ku1[r], p.ku2[r], p.anis_u[r])
+            ctx.set_material(r, p.msat[r], p.aex[r], p.alpha[r], p.gamma[r], p.ku1[r], p.ku2[r], p.anis_u[r],
+                             p.dind[r])
             ctx.set_bext(r, p.b0[r], p.b1[r])
         for i, r1 in enumerate(used):
             for r2 in used[i + 1:]:
