@@ -141,7 +141,10 @@ __host__ __device__ constexpr int ns_of(int L, int p) {
 // as it is loaded.
 // WARP: the pencils belong to one warp (NT = 32, lanes share the butterflies,
 // __syncwarp() orders reads before writes) instead of the whole block.
-template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, bool WARP = false>
+// IS: stride between the pencils of one group (default 1), so that
+// base = (q / INNER) * BS + (q % INNER) * IS.
+template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, bool WARP = false,
+          int IS = 1>
 __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw,
                                               const float2* __restrict__ pre = nullptr) {
   constexpr int NB = L / R;
@@ -154,7 +157,7 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
     const int b = tid + q * NT;
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
-      const int base = (p / INNER) * BS + (p % INNER);
+      const int base = (p / INNER) * BS + (p % INNER) * IS;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q][r] = s[base + (j + r * NB) * ES];
       if (NS == 1 && pre != nullptr) {
@@ -170,7 +173,7 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
     const int b = tid + q * NT;
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
-      const int base = (p / INNER) * BS + (p % INNER);
+      const int base = (p / INNER) * BS + (p % INNER) * IS;
       const int k = j % NS;
       if (NS > 1) {
 #pragma unroll
@@ -194,19 +197,20 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
 // Full length-L complex transform of NP shared-memory pencils (in place,
 // natural order), addressed as in stockham_pass.  Callers synchronise before
 // (data written); the last pass ends with __syncthreads().
-template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL = kTwN, int P = 0,
+template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL = kTwN, int IS = 1, int P = 0,
           bool DONE = (P >= npasses(L))>
 struct FftG;
-template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
-struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, false> {
+template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int IS, int P>
+struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, false> {
   __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw,
                                              const float2* __restrict__ pre = nullptr) {
-    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL>(s, tw, P == 0 ? pre : nullptr);
-    FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P + 1>::run(s, tw);
+    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL, false, IS>(s, tw,
+                                                                                            P == 0 ? pre : nullptr);
+    FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P + 1>::run(s, tw);
   }
 };
-template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int P>
-struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, P, true> {
+template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int IS, int P>
+struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, true> {
   __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr) {}
 };
 

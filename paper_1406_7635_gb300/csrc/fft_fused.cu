@@ -453,6 +453,150 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   if (CL > 1) cluster.sync();   // keep shared memory alive until every peer has read it
 }
 
+// k_yz for clusters split in z (clz = 2): the y transform commutes with the
+// z-class twiddle (a per-row factor), so the two blocks of a z-class pair
+// (same ry) share it.  Each block loads and y-transforms one half of the z
+// rows (its half h = rz), takes the other half from its partner through
+// distributed shared memory, and after the inverse z pass sums the pair's
+// two classes (conjugate z twiddle) for its half of the rows, so the inverse
+// y transform also runs on half the rows.  The last step adds the y classes
+// (cly = 2) as before.  Same shared-memory layout as k_yz.
+template <int LY, int LZ, int NT>
+__global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec, const float* __restrict__ kt,
+                                            const float2* __restrict__ tw, const DevState* __restrict__ st,
+                                            BatchArgs ba) {
+  if (st && st->done) return;   // uniform across the cluster (same instance and kx)
+  const int inst = blockIdx.x / (g.hx * g.cly * 2);
+  if (ba.done && ba.done[(long long)inst * ba.done_stride]) return;
+  spec += (long long)inst * 3 * g.hx * g.nz * g.ny;
+  extern __shared__ float2 s[];
+  constexpr int RP = LY + 1;
+  constexpr int CS = LZ * RP;
+  constexpr int H = LZ / 2;          // rows per z half
+  constexpr int PH = LY * H;         // points of one component's half
+  float2* twy = s + 3 * CS;
+  float2* twz = twy + LY;
+  float2* rty = twz + LZ;
+  float2* rtz = rty + LY;
+  load_twiddles<LY, NT>(twy, tw);
+  load_twiddles<LZ, NT>(twz, tw);
+  for (int i = threadIdx.x; i < LY; i += NT) rty[i] = __ldg(&tw[(i * (kTwN / g.py)) & (kTwN - 1)]);
+  for (int i = threadIdx.x; i < LZ; i += NT) rtz[i] = __ldg(&tw[(i * (kTwN / g.pz)) & (kTwN - 1)]);
+  const int CL = g.cly * 2;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int ry = rank % g.cly, rz = rank / g.cly;
+  const int zpart = ry + g.cly * (1 - rz);   // same ry, other z class
+  const int kx = (blockIdx.x / CL) % g.hx;
+  const int h0 = rz * H, ho = (1 - rz) * H;  // first row of my half, of the partner's half
+  const int cstride = g.hx * g.nz * g.ny;
+  float2* const plane = spec + kx * g.nz * g.ny;
+  // 1. load my half of the rows
+  for (int e = threadIdx.x; e < 3 * PH; e += NT) {
+    const int y = e % LY, i = (e / LY) % H, c = e / PH, z = h0 + i;
+    float2* dst = s + c * CS + z * RP + y;
+    if (y < g.ny && z < g.nz) {
+      const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr),
+                   "l"(plane + c * cstride + z * g.ny + y));
+    } else {
+      *dst = make_float2(0.f, 0.f);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  // 2. forward y on my half of the rows of all three components (pencil q:
+  //    component q / H, row h0 + q % H), y-class twiddle on load
+  FftG<LY, -1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy, ry ? rty : nullptr);
+  // 3. the partner's half, transformed by the partner
+  cluster.sync();
+  {
+    const float2* ps = cluster.map_shared_rank(s, zpart);
+    constexpr int NB = 3 * PH;
+    constexpr int PER = (NB + NT - 1) / NT;
+    float2 v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (NB % NT == 0 || e < NB) {
+        const int y = e % LY, i = (e / LY) % H, c = e / PH;
+        v[q] = ps[c * CS + (ho + i) * RP + y];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (NB % NT == 0 || e < NB) {
+        const int y = e % LY, i = (e / LY) % H, c = e / PH;
+        s[c * CS + (ho + i) * RP + y] = v[q];
+      }
+    }
+  }
+  cluster.sync();   // the partner's rows are read before anyone transforms in z
+  // 4. z: first pass (z-class twiddle on load), fused middle, last inverse pass
+  constexpr int R0 = LZ / zmid_radix(LZ);
+  if constexpr (R0 > 1) {
+    stockham_pass<LZ, R0, 1, -1, 2 * LY, NT, LY, CS, RP, LZ>(s, twz, rz ? rtz : nullptr);
+    stockham_pass<LZ, R0, 1, -1, LY, NT, LY, CS, RP, LZ>(s + 2 * CS, twz, rz ? rtz : nullptr);
+  }
+  z_mid<LY, LZ, NT, RP, CS>(s, twz, rtz, kt, g, kx, ry, rz);
+  __syncthreads();
+  z_inv_tail<LY, LZ, NT, RP, CS, 2>(s, twz);
+  z_inv_tail<LY, LZ, NT, RP, CS, 1>(s + 2 * CS, twz);
+  // 5. my half of the rows: sum of the pair's two z classes (conjugate z
+  //    twiddle; class 0 has none), in place
+  cluster.sync();
+  {
+    const float2* ps = cluster.map_shared_rank(s, zpart);
+    constexpr int NB = 3 * PH;
+    constexpr int PER = (NB + NT - 1) / NT;
+    float2 v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (NB % NT == 0 || e < NB) {
+        const int y = e % LY, i = (e / LY) % H, c = e / PH;
+        v[q] = ps[c * CS + (h0 + i) * RP + y];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (NB % NT == 0 || e < NB) {
+        const int y = e % LY, i = (e / LY) % H, c = e / PH, z = h0 + i;
+        const int a = c * CS + z * RP + y;
+        const float2 w = cconj(rtz[z]);   // the z class 1 twiddle at row z
+        s[a] = rz ? cadd(cmul(s[a], w), v[q]) : cadd(s[a], cmul(v[q], w));
+      }
+    }
+  }
+  __syncthreads();
+  // 6. inverse y on my half of the rows
+  FftG<LY, 1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy);
+  // 7. sum over the y classes (cly = 2: the block with the other ry and the
+  //    same half) and store; with cly = 2 each block stores half of its rows
+  if (g.cly > 1) cluster.sync();
+  {
+    const float2* yp = g.cly > 1 ? cluster.map_shared_rank(s, (1 - ry) + g.cly * rz) : s;
+    const int n_rows = g.cly > 1 ? H / 2 : H;           // rows of my half that I store
+    const int r0 = h0 + (g.cly > 1 ? ry * (H / 2) : 0);
+    const int nb = 3 * n_rows * LY;
+    for (int e = threadIdx.x; e < nb; e += NT) {
+      const int y = e % LY, i = (e / LY) % n_rows, c = e / (LY * n_rows), z = r0 + i;
+      if (y >= g.ny || z >= g.nz) continue;
+      const int a = c * CS + z * RP + y;
+      float2 v = s[a];
+      if (g.cly > 1) {
+        const float2 o = yp[a];
+        const float2 w = cconj(rty[y]);   // the y class 1 twiddle
+        v = ry ? cadd(cmul(v, w), o) : cadd(v, cmul(o, w));
+      }
+      plane[c * cstride + z * g.ny + y] = v;
+    }
+  }
+  cluster.sync();   // keep shared memory alive until every peer has read it
+}
+
 // rows per block of the x-row kernels: the default rule (enough blocks to
 // fill the GPU: 8 rows of <= 128 points), or half / twice it
 template <int L>
@@ -510,20 +654,22 @@ struct YzCfg {
   static constexpr size_t SMEM = sizeof(float2) * (3 * LZ * (LY + 1) + 2 * (LY + LZ));
 };
 
-template <int LY, int LZ>
-void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
-  using C = YzCfg<LY, LZ>;
-  auto kern = k_yz<LY, LZ, C::NT>;
-  static bool attr_set = false;
+// one cluster launch of a (y, z) kernel: CLY*CLZ blocks per kx plane and
+// instance; the kernel's shared-memory limit is raised on its first launch
+// (outside stream capture: the context's warm-up and the batch autotuner
+// launch every configuration first)
+template <typename K>
+void launch_yz_cluster(K kern, bool& attr_set, size_t smem, int nt, const Geom& g, const Buffers& b, cudaStream_t s,
+                       const BatchArgs& ba) {
   if (!attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
   const int CL = g.cly * g.clz;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(g.hx * CL * ba.count);
-  cfg.blockDim = dim3(C::NT);
-  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -533,6 +679,21 @@ void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st, ba);
+}
+
+template <int LY, int LZ>
+void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
+  using C = YzCfg<LY, LZ>;
+  if constexpr (LZ >= 4) {
+    // z-split clusters share the y transforms between the two z classes
+    if (g.clz == 2) {
+      static bool set2 = false;
+      launch_yz_cluster(k_yz2<LY, LZ, C::NT>, set2, C::SMEM, C::NT, g, b, s, ba);
+      return;
+    }
+  }
+  static bool set1 = false;
+  launch_yz_cluster(k_yz<LY, LZ, C::NT>, set1, C::SMEM, C::NT, g, b, s, ba);
 }
 
 __global__ void k_kt_transpose(Geom g, const float* __restrict__ kt, float* __restrict__ ktf) {

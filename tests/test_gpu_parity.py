@@ -75,6 +75,10 @@ GRIDS = [
     ((3, 300, 20), (2e-9, 2e-9, 4e-9)),     # fused path, residue split in y (2 blocks)
     ((20, 100, 40), (3e-9, 3e-9, 2e-9)),    # fused path, split in y and z (4 blocks)
     ((40, 30, 9), (2e-9, 2e-9, 2e-9)),      # general path (pz too large for the fused plane)
+    ((1, 3, 1024), (1e-9, 2e-9, 1e-9)),     # maximum nx (px = 2048, the twiddle table's length)
+    ((1, 512, 6), (2e-9, 1e-9, 1e-9)),      # maximum ny
+    ((512, 2, 3), (1e-9, 1e-9, 0.5e-9)),    # maximum nz
+    ((2, 512, 512), (2e-9, 2e-9, 1e-9)),    # largest fused plane side (lx = 512, ly = 1024)
 ]
 
 
