@@ -22,28 +22,20 @@ Readings where the paper is silent:
 """
 import numpy as np
 
-from .field import exchange_lut, msat_cells
+from .field import exchange_lut, msat_cells, neighbour_of, periodic_axes
 
 
 def _neighbour(p, m, axis, step):
     """Neighbour values along `axis` (2 = x, 1 = y, 0 = z of the (z, y, x)
     arrays) in direction `step` (+1 / -1): the neighbour's m where it exists
-    and is magnetic, else the ghost value of the central cell.  Returns
-    (values (3, nz, ny, nx), present mask)."""
+    and is magnetic (wrapping around along a periodic axis), else the ghost
+    value of the central cell.  Returns (values (3, nz, ny, nx), present
+    mask)."""
     mag = p.magnetic()
-    n = m.shape[1 + axis]
-    nb = np.zeros_like(m)
-    present = np.zeros(mag.shape, dtype=bool)
-    sl_c = [slice(None)] * 3
-    sl_n = [slice(None)] * 3
-    if step == 1:
-        sl_c[axis], sl_n[axis] = slice(0, n - 1), slice(1, n)
-    else:
-        sl_c[axis], sl_n[axis] = slice(1, n), slice(0, n - 1)
-    sl_c, sl_n = tuple(sl_c), tuple(sl_n)
-    present[sl_c] = mag[sl_n]
-    for c in range(3):
-        nb[c][sl_c] = m[c][sl_n]
+    per = periodic_axes(p)[axis]
+    nmag, valid = neighbour_of(mag, axis, step, per)
+    present = nmag & valid
+    nb = np.stack([neighbour_of(m[c], axis, step, per)[0] for c in range(3)])
     # ghosts: m + step * Delta * dm/d(axis) at the boundary
     d = p.dind[p.region]
     a = p.aex[p.region]

@@ -25,31 +25,55 @@ def exchange_lut(p):
     return 2.0 * p.exch_scale * h
 
 
+def periodic_axes(p):
+    """Periodic flags per array axis (0 = z, 1 = y, 2 = x) of the (z, y, x)
+    arrays, from p.pbc = (Px, Py, Pz)."""
+    px, py, pz = getattr(p, "pbc", (0, 0, 0))
+    return (pz > 0, py > 0, px > 0)
+
+
+def neighbour_of(a, axis, step, periodic):
+    """a shifted so that entry i holds a[i + step] along `axis`, wrapping
+    around on a periodic axis; returns (values, valid) where valid marks the
+    entries that have a neighbour (all of them on a periodic axis)."""
+    n = a.shape[axis]
+    if periodic:
+        return np.roll(a, -step, axis=axis), np.ones(a.shape, dtype=bool)
+    out = np.zeros_like(a)
+    valid = np.zeros(a.shape, dtype=bool)
+    sl_c = [slice(None)] * a.ndim
+    sl_n = [slice(None)] * a.ndim
+    if step == 1:
+        sl_c[axis], sl_n[axis] = slice(0, n - 1), slice(1, n)
+    else:
+        sl_c[axis], sl_n[axis] = slice(1, n), slice(0, n - 1)
+    out[tuple(sl_c)] = a[tuple(sl_n)]
+    valid[tuple(sl_c)] = True
+    return out, valid
+
+
 def exchange_field(p, m):
     """6-neighbour exchange: sum over neighbours of lut * (m_i - m) / Delta_i^2.
 
     A neighbour outside the grid or not magnetic is missing; using the cell's
     own m in its place (Neumann condition, Sec. III.C) makes its term zero.
+    Along a periodic axis the grid wraps around (the paper's PBC are felt by
+    the stencils), so the first and last cells are neighbours.
     """
     mag = p.magnetic()
     lut = exchange_lut(p)
     reg = p.region.astype(np.int64)
+    per = periodic_axes(p)
     B = np.zeros_like(m)
     for axis, delta in ((2, p.dx), (1, p.dy), (0, p.dz)):
-        n = m.shape[1 + axis]
         for step in (1, -1):
-            # cell i (sl_c) and its neighbour i + step (sl_n) along this axis
-            sl_c = [slice(None)] * 3
-            sl_n = [slice(None)] * 3
-            if step == 1:
-                sl_c[axis], sl_n[axis] = slice(0, n - 1), slice(1, n)
-            else:
-                sl_c[axis], sl_n[axis] = slice(1, n), slice(0, n - 1)
-            sl_c, sl_n = tuple(sl_c), tuple(sl_n)
-            both = mag[sl_c] & mag[sl_n]
-            coupling = np.where(both, lut[reg[sl_c], reg[sl_n]], 0.0)
+            nreg, valid = neighbour_of(reg, axis, step, per[axis])
+            nmag, _ = neighbour_of(mag, axis, step, per[axis])
+            both = mag & nmag & valid
+            coupling = np.where(both, lut[reg, nreg], 0.0)
             for c in range(3):
-                B[c][sl_c] += coupling * (m[c][sl_n] - m[c][sl_c]) / delta ** 2
+                nm, _ = neighbour_of(m[c], axis, step, per[axis])
+                B[c] += coupling * (nm - m[c]) / delta ** 2
     return B * mag[None]
 
 
@@ -84,10 +108,11 @@ def effective_field(p, m, t, demag_method="fft", spectrum=None):
     terms = {}
     if p.demag:
         M = magnetisation(msat_cells(p), m)
+        pbc = getattr(p, "pbc", (0, 0, 0))
         if demag_method == "direct":
-            terms["demag"] = demag_direct(M, p.dx, p.dy, p.dz)
+            terms["demag"] = demag_direct(M, p.dx, p.dy, p.dz, pbc)
         else:
-            terms["demag"] = demag_fft(M, p.dx, p.dy, p.dz, spectrum=spectrum)
+            terms["demag"] = demag_fft(M, p.dx, p.dy, p.dz, spectrum=spectrum, pbc=pbc)
     else:
         terms["demag"] = zero
     has_dmi = bool(np.any(p.dind[np.unique(p.region)] != 0))
@@ -144,7 +169,7 @@ class Field:
         self.spectrum = None
         if p.demag and demag_method == "fft":
             from .demag import kernel_spectrum
-            self.spectrum = kernel_spectrum(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
+            self.spectrum = kernel_spectrum(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, getattr(p, "pbc", (0, 0, 0)))
         self.evals = 0
 
     def terms(self, m, t):

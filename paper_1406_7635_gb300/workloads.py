@@ -57,6 +57,7 @@ class Problem:
     anis: bool = True
     zeeman: bool = True
     precession: bool = True
+    pbc: tuple = (0, 0, 0)         # periodic images on each side along x, y, z (0 = open)
     m0: np.ndarray = None          # float64 (3, nz, ny, nx), unit or zero
     # solver settings (Sec. IV: MaxErr default 1e-5, headroom 0.8)
     max_err: float = 1e-5
