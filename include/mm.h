@@ -112,6 +112,16 @@ int mm_set_bext_timefn(mm_ctx* ctx, double freq, double phase);
 int mm_enable_terms(mm_ctx* ctx, int demag, int exch, int anis, int zeeman,
                     int precession);
 
+/* Periodic boundary conditions (Sec. III.B, "Periodic boundary
+ * conditions"), macro geometry: px, py, pz images of the box on each side
+ * along x, y, z (0 = open axis).  A source image contributes to a cell when
+ * its offset along the periodic axis lies within -P n < D < P n (n cells);
+ * the convolution along that axis becomes cyclic (no padding) and the
+ * exchange and DMI stencils wrap around.  A periodic axis needs 1 cell or a
+ * power of two >= 4 cells (else MM_ERR_ARG).  Rebuilds the demag kernel;
+ * keeps m, t, the materials and the geometry mask.  (0, 0, 0) at creation. */
+int mm_set_pbc(mm_ctx* ctx, int px, int py, int pz);
+
 /* Reduced magnetisation m, float32 SoA [3][nz][ny][nx].  The library
  * normalises it per magnetic cell and zeroes it in vacuum.  Setting m
  * invalidates the cached first RK stage. */

@@ -280,8 +280,6 @@ constexpr int kT = 256;
 
 }  // namespace
 
-Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz);
-
 struct BClass {
   Geom g{};
   int B = 0;

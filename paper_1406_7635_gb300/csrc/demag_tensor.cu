@@ -174,6 +174,36 @@ __global__ void k_tensor_octant(int nx, int ny, int nz, double dx, double dy, do
   for (int c = 0; c < 6; ++c) w[c * n + i] = v[c];
 }
 
+// First octant of the periodic (macro-geometry) kernel, Sec. III.B: extents
+// (mx, my, mz) = n/2 + 1 along a periodic axis, n along an open one; along a
+// periodic axis of n cells with P images per side the value at offset X is
+// the tensor summed over the offsets D = X + k n with |D| < P n.
+__global__ void k_tensor_octant_pbc(int mx, int my, int mz, int nx, int ny, int nz, int pbx, int pby, int pbz,
+                                    double dx, double dy, double dz, GLRules gl, double* __restrict__ w) {
+  const long long n = (long long)mx * my * mz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int X = (int)(i % mx), Y = (int)((i / mx) % my), Z = (int)(i / ((long long)mx * my));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const int kx = pbx > 0 ? pbx : 0, ky = pby > 0 ? pby : 0, kz = pbz > 0 ? pbz : 0;
+  for (int a = -kx; a <= kx; ++a) {
+    const long long DX = X + (long long)a * nx;
+    if (pbx > 0 && !(DX > -(long long)pbx * nx && DX < (long long)pbx * nx)) continue;
+    for (int b = -ky; b <= ky; ++b) {
+      const long long DY = Y + (long long)b * ny;
+      if (pby > 0 && !(DY > -(long long)pby * ny && DY < (long long)pby * ny)) continue;
+      for (int c = -kz; c <= kz; ++c) {
+        const long long DZ = Z + (long long)c * nz;
+        if (pbz > 0 && !(DZ > -(long long)pbz * nz && DZ < (long long)pbz * nz)) continue;
+        double v[6];
+        tensor_at(DX * dx, DY * dy, DZ * dz, dx, dy, dz, gl, v);
+        for (int t = 0; t < 6; ++t) acc[t] += v[t];
+      }
+    }
+  }
+  for (int t = 0; t < 6; ++t) w[t * n + i] = acc[t];
+}
+
 // Parity (odd = 1) of component c along axis a (0 x, 1 y, 2 z).
 __host__ __device__ inline int odd_axis(int c, int a) {
   // Nxy odd in x,y; Nxz odd in x,z; Nyz odd in y,z; diagonals even
@@ -229,7 +259,9 @@ void axis_tables(int n, int P, int h, std::vector<double>& tc, std::vector<doubl
     for (int X = 0; X < n; ++X) {
       const long long num = (2LL * k * X) % (2LL * P);   // angle = pi * num / P
       const double ang = kPi * (double)num / (double)P;
-      tc[(size_t)k * n + X] = (X == 0 ? 1.0 : 2.0) * std::cos(ang);
+      // offsets X and -X are distinct points of the cyclic axis unless
+      // X = 0 or X = P/2 (a periodic axis reaches its Nyquist offset)
+      tc[(size_t)k * n + X] = (X == 0 || 2 * X == P ? 1.0 : 2.0) * std::cos(ang);
       ts[(size_t)k * n + X] = 2.0 * std::sin(ang);
     }
 }
@@ -242,7 +274,7 @@ __global__ void k_axis_tables(int n, int P, int h, double* __restrict__ tc, doub
   const int k = i / n, X = i % n;
   const long long num = (2LL * k * X) % (2LL * P);   // angle = pi * num / P
   const double a = (double)num / (double)P;
-  tc[i] = (X == 0 ? 1.0 : 2.0) * cospi(a);
+  tc[i] = (X == 0 || 2 * X == P ? 1.0 : 2.0) * cospi(a);
   ts[i] = 2.0 * sinpi(a);
 }
 
@@ -258,8 +290,10 @@ cudaError_t demag_tensor_offsets(int n, const int32_t* d_off, double dx, double 
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
                                   cudaStream_t s) {
   const GLRules gl = make_gl_rules();
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const long long n = g.n;
+  // octant extents: n along an open axis, n/2 + 1 along a periodic one
+  const bool pbc = g.pbcx > 0 || g.pbcy > 0 || g.pbcz > 0;
+  const int nx = g.pbcx > 0 ? g.hkx : g.nx, ny = g.pbcy > 0 ? g.hky : g.ny, nz = g.pbcz > 0 ? g.hkz : g.nz;
+  const long long n = (long long)nx * ny * nz;
   const int hx = g.hkx, hy = g.hky, hz = g.hkz;
   // work buffers sized for the largest intermediate
   const long long cap = 6LL * std::max<long long>(
@@ -276,7 +310,11 @@ cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz
   }
   const int T = 128;
   auto blocks = [&](long long tot) { return (unsigned)((tot + T - 1) / T); };
-  k_tensor_octant<<<blocks(n), T, 0, s>>>(nx, ny, nz, dx, dy, dz, gl, w0);
+  if (pbc)
+    k_tensor_octant_pbc<<<blocks(n), T, 0, s>>>(nx, ny, nz, g.nx, g.ny, g.nz, g.pbcx, g.pbcy, g.pbcz, dx, dy, dz,
+                                                 gl, w0);
+  else
+    k_tensor_octant<<<blocks(n), T, 0, s>>>(nx, ny, nz, dx, dy, dz, gl, w0);
 
   std::vector<double> tc, ts;
   auto transform = [&](int len, int P, int h, long long outer, int axis, double* in, double* out) {

@@ -141,9 +141,14 @@ __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const 
   if (T.exch || T.dmi) {
     const float* __restrict__ xl = b.xlut + r * kXStride;
     const int sy = g.nx, sz = g.nx * g.ny, n = (int)g.n;
-    const int js[6] = {x > 0 ? i - 1 : i,          x < g.nx - 1 ? i + 1 : i,
-                             y > 0 ? i - sy : i,         y < g.ny - 1 ? i + sy : i,
-                             z > 0 ? i - sz : i,         z < g.nz - 1 ? i + sz : i};
+    // along a periodic axis the grid wraps around (Sec. III.B, PBC)
+    const int js[6] = {x > 0 ? i - 1 : (g.pbcx ? i + g.nx - 1 : i),
+                       x < g.nx - 1 ? i + 1 : (g.pbcx ? i - (g.nx - 1) : i),
+                       y > 0 ? i - sy : (g.pbcy ? i + sy * (g.ny - 1) : i),
+                       y < g.ny - 1 ? i + sy : (g.pbcy ? i - sy * (g.ny - 1) : i),
+                       z > 0 ? i - sz : (g.pbcz ? i + sz * (g.nz - 1) : i),
+                       z < g.nz - 1 ? i + sz : (g.pbcz ? i - sz * (g.nz - 1) : i)};
+    const bool per[6] = {g.pbcx > 0, g.pbcx > 0, g.pbcy > 0, g.pbcy > 0, g.pbcz > 0, g.pbcz > 0};
     const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
     if (!T.dmi) {
 #pragma unroll
@@ -163,7 +168,7 @@ __device__ __forceinline__ void field_at(const Geom& g, const Buffers& b, const 
       for (int d = 0; d < 6; ++d) {
         const int j = js[d];
         const int cj = b.code[j];
-        const bool present = j != i && cj != kVacuum;
+        const bool present = (j != i || per[d]) && cj != kVacuum;
         const float3 mj = present ? f3(m[j], m[n + j], m[2 * n + j]) : dmi_ghost(mi, d, cbc, g.cdx, g.cdy);
         const float c = T.exch ? __ldg(&xl[present ? cj : r]) * id2[d] : 0.0f;
         ex.x += c * (mj.x - mi.x);

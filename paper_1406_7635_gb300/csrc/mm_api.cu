@@ -172,7 +172,9 @@ void enqueue_demag(mm_ctx* c) {
 
 // The row-stage path (fused convolution layout, exact demag): per attempt one
 // prep kernel, then per stage the (y, z) transform and one row kernel.
-bool rowstage_path(const mm_ctx* c) { return c->g.fused && !c->sur_active && c->method == 0; }
+// (a periodic x axis has no padding, so its rows do not fit the row
+// kernels' shared-memory stencil, which holds px / 2 cells per row)
+bool rowstage_path(const mm_ctx* c) { return c->g.fused && !c->sur_active && c->method == 0 && c->g.pbcx == 0; }
 
 // stage-1 torque at the current m (FSAL start)
 void enqueue_k1(mm_ctx* c) {
@@ -298,8 +300,13 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 
 // Grid and padded-FFT geometry of an nx x ny x nz grid (the fused-path
 // fields are filled in by fused_plan).
-Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz) {
+Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz, const int* pbc) {
   Geom g{};
+  if (pbc) {
+    g.pbcx = pbc[0];
+    g.pbcy = pbc[1];
+    g.pbcz = pbc[2];
+  }
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
@@ -309,9 +316,11 @@ Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz) {
   g.cdy = (float)dy;
   g.idy2 = (float)(1.0 / (dy * dy));
   g.idz2 = (float)(1.0 / (dz * dz));
-  g.px = nx == 1 ? 1 : next_pow2(2 * nx - 1);
-  g.py = ny == 1 ? 1 : next_pow2(2 * ny - 1);
-  g.pz = nz == 1 ? 1 : next_pow2(2 * nz - 1);
+  // transform lengths: a periodic axis is cyclic with period n (Sec. III.B,
+  // periodic boundary conditions), an open axis zero-padded to 2n - 1 or more
+  g.px = nx == 1 ? 1 : (g.pbcx > 0 ? nx : next_pow2(2 * nx - 1));
+  g.py = ny == 1 ? 1 : (g.pbcy > 0 ? ny : next_pow2(2 * ny - 1));
+  g.pz = nz == 1 ? 1 : (g.pbcz > 0 ? nz : next_pow2(2 * nz - 1));
   g.lx = g.px == 1 ? 1 : g.px / 2;
   g.hx = g.px == 1 ? 1 : g.lx + 1;
   g.hxs = (g.hx + 7) / 8 * 8;
@@ -729,6 +738,55 @@ int mm_get_energies(mm_ctx* c, mm_energies* out) {
   out->dmi = acc[8] * V;
   out->total = out->demag + out->exch + out->anis + out->zeeman + out->dmi;
   for (int k = 0; k < 3; ++k) out->m_avg[k] = acc[7] > 0 ? acc[4 + k] / acc[7] : 0.0;
+  return MM_OK;
+}
+
+int mm_set_pbc(mm_ctx* c, int px, int py, int pz) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  const int pbc[3] = {px, py, pz};
+  const int n[3] = {c->g.nx, c->g.ny, c->g.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (pbc[a] < 0 || pbc[a] > 4096) return fail(MM_ERR_ARG, "periodic images must be 0..4096");
+    const bool pow2 = (n[a] & (n[a] - 1)) == 0;
+    if (pbc[a] > 0 && n[a] != 1 && (n[a] < 4 || !pow2))
+      return fail(MM_ERR_ARG, "a periodic axis needs 1 cell or a power of two >= 4 cells");
+  }
+  Geom g = make_geom(c->g.nx, c->g.ny, c->g.nz, c->dx, c->dy, c->dz, pbc);
+  fused_plan(g);
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  // buffers whose size depends on the transform lengths
+  Buffers& b = c->b;
+  void* old[] = {b.spec, b.kt, b.ktf, b.ms2};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  b.spec = nullptr;
+  b.kt = b.ktf = nullptr;
+  b.ms2 = nullptr;
+  c->graph_valid = false;
+  c->k1_valid = false;
+  const size_t vec = 3 * (size_t)g.n * sizeof(float);
+  cudaError_t e = cudaMalloc((void**)&b.spec, 3 * (size_t)g.sc * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.spec, 0, 3 * (size_t)g.sc * sizeof(float2), c->stream);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b.kt, 6 * (size_t)g.hkx * g.hky * g.hkz * sizeof(float));
+  if (e == cudaSuccess && g.fused) e = cudaMalloc((void**)&b.ktf, 6 * (size_t)g.hkx * g.hky * g.hkz * sizeof(float));
+  if (e == cudaSuccess && g.fused) e = cudaMalloc((void**)&b.ms2, vec);
+  if (e == cudaSuccess && g.fused) e = cudaMemsetAsync(b.ms2, 0, vec, c->stream);
+  if (e == cudaSuccess) e = build_kernel_spectrum(g, c->dx, c->dy, c->dz, b.kt, c->stream);
+  if (e == cudaSuccess && g.fused) launch_kt_transpose(g, b.kt, b.ktf, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  c->g = g;
+  if (e == cudaSuccess) {
+    // one convolution outside any capture (launch attributes), as at creation
+    Buffers nb = b;
+    nb.st = nullptr;
+    launch_demag(g, nb, b.ms, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && g.fused && g.pbcx == 0) e = prepare_rowstage(g);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,
+                std::string("set_pbc: ") + cudaGetErrorString(e));
   return MM_OK;
 }
 

@@ -47,6 +47,7 @@ struct Geom {
   int fused, cly, clz, ly, lz;
   int xrows;              // x-row kernels: rows per block (0 = default rule)
   float cdx, cdy;         // cell sizes along x and y (DMI ghost values)
+  int pbcx, pbcy, pbcz;   // periodic images on each side (0 = open axis)
 };
 
 // Integrator state on the device (one per context).  Every kernel of a step
@@ -97,7 +98,8 @@ struct Buffers {
 // enabled field terms; dmi is set by the library when a region has D != 0
 struct Terms { int demag, exch, anis, zeeman, dmi; };
 
-Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz);
+// pbc (may be null): periodic images per axis; a periodic axis is not padded
+Geom make_geom(int nx, int ny, int nz, double dx, double dy, double dz, const int* pbc = nullptr);
 
 // Instance dimension of the fused convolution kernels: `count` instances of
 // one grid laid out back to back; optional per-instance Msat (every cell

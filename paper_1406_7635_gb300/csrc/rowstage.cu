@@ -142,7 +142,10 @@ __device__ __forceinline__ void stage_stencil(const Geom& g, const float* __rest
         const int q = lr - (ROWS + 2);
         yy = y0 + (q % ROWS);
         zz = q < ROWS ? z - 1 : z + 1;
+      } else if (g.pbcy) {
+        yy = (yy + g.ny) % g.ny;          // halo rows wrap around a periodic y
       }
+      if (g.pbcz) zz = (zz + g.nz) % g.nz;
       if (4 * ch >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
       const int row = (zz * g.ny + yy) * g.nx + 4 * ch;
       const void* src = a < 3 ? (const void*)(ms + a * n + row) : (const void*)(code + row);
@@ -157,7 +160,10 @@ __device__ __forceinline__ void stage_stencil(const Geom& g, const float* __rest
         const int q = lr - (ROWS + 2);
         yy = y0 + (q % ROWS);
         zz = q < ROWS ? z - 1 : z + 1;
+      } else if (g.pbcy) {
+        yy = (yy + g.ny) % g.ny;
       }
+      if (g.pbcz) zz = (zz + g.nz) % g.nz;
       if (ch >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
       const int row = (zz * g.ny + yy) * g.nx + ch;
       const void* src = a < 3 ? (const void*)(ms + a * n + row) : (const void*)(code + row);
@@ -300,12 +306,14 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     if (T.exch || T.dmi) {
       // same neighbour order and arithmetic as field_at
       const float* __restrict__ xl = b.xlut + ci * kXStride;
-      const int nb[6] = {x > 0 ? C - 1 : C,
-                         x < g.nx - 1 ? C + 1 : C,
-                         y > 0 ? C - L : C,
-                         y < g.ny - 1 ? C + L : C,
-                         z > 0 ? (ROWS + 2 + r) * L + x : C,
-                         z < g.nz - 1 ? (2 * ROWS + 2 + r) * L + x : C};
+      // periodic axes wrap: the staged halo rows/planes hold the wrapped data
+      const int nb[6] = {x > 0 ? C - 1 : (g.pbcx ? C + g.nx - 1 : C),
+                         x < g.nx - 1 ? C + 1 : (g.pbcx ? C - (g.nx - 1) : C),
+                         (y > 0 || g.pbcy) ? C - L : C,
+                         (y < g.ny - 1 || g.pbcy) ? C + L : C,
+                         (z > 0 || g.pbcz) ? (ROWS + 2 + r) * L + x : C,
+                         (z < g.nz - 1 || g.pbcz) ? (2 * ROWS + 2 + r) * L + x : C};
+      const bool per[6] = {g.pbcx > 0, g.pbcx > 0, g.pbcy > 0, g.pbcy > 0, g.pbcz > 0, g.pbcz > 0};
       const float id2[6] = {g.idx2, g.idx2, g.idy2, g.idy2, g.idz2, g.idz2};
       if (!T.dmi) {
 #pragma unroll
@@ -324,7 +332,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
         for (int d = 0; d < 6; ++d) {
           const int j = nb[d];
           const int cj = scode[j];
-          const bool present = j != C && cj != kVacuum;
+          const bool present = (j != C || per[d]) && cj != kVacuum;
           const float3 mj = present ? f3(sten[j], sten[NR * L + j], sten[2 * NR * L + j])
                                     : dmi_ghost(mi, d, cbc, g.cdx, g.cdy);
           const float c = T.exch ? __ldg(&xl[present ? cj : ci]) * id2[d] : 0.0f;

@@ -87,6 +87,7 @@ _SIGS = {
     "mm_get_energies": (_I, [_P, C.POINTER(mm_energies)]),
     "mm_get_stats": (_I, [_P, C.POINTER(mm_stats)]),
     "mm_get_max_torque": (_I, [_P, C.POINTER(_D)]),
+    "mm_set_pbc": (_I, [_P, _I, _I, _I]),
     "mm_set_integrator": (_I, [_P, _I]),
     "mm_get_integrator": (_I, [_P, C.POINTER(_I)]),
     "mm_relax": (_I, [_P, C.c_longlong, C.POINTER(C.c_longlong)]),
@@ -269,6 +270,9 @@ class Context:
         return {"total": e.total, "demag": e.demag, "exch": e.exch, "anis": e.anis, "zeeman": e.zeeman,
                 "dmi": e.dmi, "m_avg": list(e.m_avg)}
 
+    def set_pbc(self, px, py, pz):
+        _check(mm_set_pbc(self.h, int(px), int(py), int(pz)))
+
     def get_max_torque(self):
         v = C.c_double()
         _check(mm_get_max_torque(self.h, C.byref(v)))
@@ -338,6 +342,8 @@ class Context:
     @classmethod
     def from_problem(cls, p, device=0, stream=None, regions_used=None):
         ctx = cls(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, device, stream)
+        if any(getattr(p, "pbc", (0, 0, 0))):
+            ctx.set_pbc(*p.pbc)
         ctx.set_geometry(p.mask)
         ctx.set_regions(p.region)
         used = np.unique(p.region) if regions_used is None else regions_used
