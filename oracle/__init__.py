@@ -21,6 +21,7 @@ paper ("The design and verification of Mumax3", Vansteenkiste et al.) by eye:
   (Eq. eqLLG).
 * ``dmi``     -- interfacial Dzyaloshinskii-Moriya field and its boundary
   conditions (Sec. III).
+* ``stt``     -- Zhang-Li and Slonczewski spin-transfer torques (Sec. III).
 * ``rk45``    -- Dormand-Prince RK45 with the adaptive step control of Sec. IV.
 * ``relax``   -- Bogacki-Shampine RK23 and relax() (Sec. IV).
 * ``fno``     -- the Fourier-neural-operator surrogate of the demag field

@@ -177,4 +177,8 @@ class Field:
 
     def torque(self, m, t):
         self.evals += 1
-        return ll_torque(self.p, m, self.terms(m, t)["total"])
+        tq = ll_torque(self.p, m, self.terms(m, t)["total"])
+        if getattr(self.p, "zhang_li", False) or getattr(self.p, "slonczewski", False):
+            from .stt import stt_torque
+            tq = tq + stt_torque(self.p, m)
+        return tq

@@ -46,6 +46,18 @@ class Problem:
     ku1: np.ndarray = field(default_factory=lambda: _zeros256())
     ku2: np.ndarray = field(default_factory=lambda: _zeros256())
     dind: np.ndarray = field(default_factory=lambda: _zeros256())   # interfacial DMI constant D (J/m^2)
+    # spin-transfer torque parameters per region: current density (A/m^2),
+    # Zhang-Li non-adiabaticity xi; Slonczewski polarisation P, Lambda,
+    # secondary parameter eps', fixed-layer direction and free-layer thickness
+    jcur: np.ndarray = field(default_factory=lambda: _zeros256(3))
+    xi: np.ndarray = field(default_factory=lambda: _zeros256())
+    pol: np.ndarray = field(default_factory=lambda: _zeros256())
+    lam: np.ndarray = field(default_factory=lambda: np.ones(256))
+    epsp: np.ndarray = field(default_factory=lambda: _zeros256())
+    mp: np.ndarray = field(default_factory=lambda: np.tile([0.0, 0.0, 1.0], (256, 1)))
+    tfree: np.ndarray = field(default_factory=lambda: _zeros256())
+    zhang_li: bool = False
+    slonczewski: bool = False
     anis_u: np.ndarray = field(default_factory=lambda: np.tile([1.0, 0.0, 0.0], (256, 1)))
     exch_scale: np.ndarray = field(default_factory=lambda: np.ones((256, 256)))
     b0: np.ndarray = field(default_factory=lambda: _zeros256(3))
