@@ -59,6 +59,15 @@ typedef struct {
                        neighbour (grid edge or vacuum) the Rohart boundary
                        conditions give a ghost value, used by exchange too.
                        D and Aex of the cell's own region; 0 = no DMI        */
+  /* spin-transfer torques (Sec. III "Zhang-Li spin-transfer torque",
+     "Slonczewski spin-transfer torque"; switched on by mm_enable_stt)       */
+  double jcur[3];   /* current density j (A/m^2)                              */
+  double xi;        /* Zhang-Li non-adiabaticity                              */
+  double pol;       /* Slonczewski spin polarisation P                        */
+  double lambda_sl; /* Slonczewski Lambda (>= 1 typical; 1 = angle-independent) */
+  double eps_prime; /* Slonczewski secondary parameter eps'                   */
+  double mp[3];     /* fixed-layer magnetisation direction (normalised)       */
+  double tfree;     /* free-layer thickness d (m); 0 = no Slonczewski torque  */
 } mm_material;
 
 typedef struct {
@@ -121,6 +130,18 @@ int mm_enable_terms(mm_ctx* ctx, int demag, int exch, int anis, int zeeman,
  * power of two >= 4 cells (else MM_ERR_ARG).  Rebuilds the demag kernel;
  * keeps m, t, the materials and the geometry mask.  (0, 0, 0) at creation. */
 int mm_set_pbc(mm_ctx* ctx, int px, int py, int pz);
+
+/* Spin-transfer torques added to dm/dt (off at creation): Zhang-Li,
+ * dm/dt -= 1/(1+a^2)((1 + xi a) m x (m x h) + (xi - a) m x h) with
+ * h = (u.grad) m, u = mu_B j / (2 e Msat (1 + xi^2)), central differences
+ * (a missing neighbour is the cell itself; periodic axes wrap); Slonczewski,
+ * dm/dt -= gamma beta/(1+a^2) ((eps - a eps') m x (m_P x m) - (eps' - a eps)
+ * m x m_P), beta = j_z hbar / (Msat e d), eps = P L^2 / ((L^2+1) + (L^2-1)
+ * m.m_P).  The printed torques are read in the sign convention of the LL
+ * torque (dm/dt = -gamma tau).  A torque is active only in regions with
+ * Msat > 0 and j != 0 (Slonczewski also needs tfree > 0 and j_z != 0); while
+ * one is active the context steps with the general stage kernels. */
+int mm_enable_stt(mm_ctx* ctx, int zhang_li, int slonczewski);
 
 /* Reduced magnetisation m, float32 SoA [3][nz][ny][nx].  The library
  * normalises it per magnetic cell and zeroes it in vacuum.  Setting m

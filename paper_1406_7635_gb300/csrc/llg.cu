@@ -43,8 +43,8 @@ __global__ void k_stage_input(Geom g, Ptrs p, float* __restrict__ ms, const DevS
   ms[2 * n + i] = acc[2];
 }
 
-__global__ void k_torque(Geom g, Buffers b, Terms T, Ptrs p, const DevState* __restrict__ st, int s, double freq,
-                         double phase_over_pi) {
+__global__ void k_torque(Geom g, Buffers b, Terms T, Stt S, Ptrs p, const DevState* __restrict__ st, int s,
+                         double freq, double phase_over_pi) {
   if (st->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
   const int n = (int)g.n;
@@ -62,7 +62,8 @@ __global__ void k_torque(Geom g, Buffers b, Terms T, Ptrs p, const DevState* __r
   const float sinft = T.zeeman ? excitation(freq, phase_over_pi, st->stage_t[s]) : 0.0f;
   FieldParts P;
   field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[n + i], b.bd[2 * n + i]), P);
-  const float3 tq = llg_torque(mi, total(P), b.lut->gfac[r], b.lut->alpha[r], st->precession);
+  const float3 tq = add_stt(g, b, S, m, i, x, y, z, r, mi,
+                            llg_torque(mi, total(P), b.lut->gfac[r], b.lut->alpha[r], st->precession));
   k[i] = tq.x;
   k[n + i] = tq.y;
   k[2 * n + i] = tq.z;
@@ -141,8 +142,8 @@ __global__ void k_error_control(Geom g, Buffers b, Ptrs p, DevState* __restrict_
 // (M.B sums; the host multiplies by the cell volume), mode 4 the maximum of
 // |torque| over the magnetic cells into the first 4 bytes of acc (float bits,
 // atomicMax; the host zeroes them first).
-__global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict__ m, const DevState* __restrict__ st,
-                            int mode, double freq, double phase_over_pi) {
+__global__ void k_field_out(Geom g, Buffers b, Terms T, Stt S, const float* __restrict__ m,
+                            const DevState* __restrict__ st, int mode, double freq, double phase_over_pi) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28, 3 n < 2^31
   const int n = (int)g.n;
   double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -159,9 +160,11 @@ __global__ void k_field_out(Geom g, Buffers b, Terms T, const float* __restrict_
       field_at(g, b, T, m, i, x, y, z, r, mi, sinft, f3(b.bd[i], b.bd[n + i], b.bd[2 * n + i]), P);
       const float3 B = total(P);
       if (mode == 0) out = B;
-      else if (mode == 1) out = llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession);
+      else if (mode == 1)
+        out = add_stt(g, b, S, m, i, x, y, z, r, mi, llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession));
       else if (mode == 4) {
-        const float3 tq = llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession);
+        const float3 tq =
+            add_stt(g, b, S, m, i, x, y, z, r, mi, llg_torque(mi, B, b.lut->gfac[r], b.lut->alpha[r], st->precession));
         tmax = sqrtf(tq.x * tq.x + tq.y * tq.y + tq.z * tq.z);
         if (!(tmax <= FLT_MAX)) tmax = __int_as_float(0x7f800000);
       } else {
@@ -257,18 +260,18 @@ void launch_stage_input(const Geom& g, const Buffers& b, int stage, cudaStream_t
   k_stage_input<<<blocks(g.n), kT, 0, s>>>(g, ptrs(b), b.ms, b.st, coef(b), stage);
 }
 
-void launch_torque_t(const Geom& g, const Buffers& b, const Terms& T, int stage, double freq, double phase,
-                     cudaStream_t s) {
-  k_torque<<<blocks(g.n), kT, 0, s>>>(g, b, T, ptrs(b), b.st, stage, freq, phase / 3.14159265358979323846);
+void launch_torque_t(const Geom& g, const Buffers& b, const Terms& T, const Stt& S, int stage, double freq,
+                     double phase, cudaStream_t s) {
+  k_torque<<<blocks(g.n), kT, 0, s>>>(g, b, T, S, ptrs(b), b.st, stage, freq, phase / 3.14159265358979323846);
 }
 
 void launch_error_control(const Geom& g, const Buffers& b, cudaStream_t s) {
   k_error_control<<<blocks(g.n), kT, 0, s>>>(g, b, ptrs(b), b.st, coef(b));
 }
 
-void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const float* m, int mode, double freq,
-                        double phase, cudaStream_t s) {
-  k_field_out<<<blocks(g.n), kT, 0, s>>>(g, b, T, m, b.st, mode, freq, phase / 3.14159265358979323846);
+void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const Stt& S, const float* m, int mode,
+                        double freq, double phase, cudaStream_t s) {
+  k_field_out<<<blocks(g.n), kT, 0, s>>>(g, b, T, S, m, b.st, mode, freq, phase / 3.14159265358979323846);
 }
 
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s) {

@@ -189,6 +189,76 @@ __device__ __forceinline__ float3 total(const FieldParts& P) {
             P.demag.z + P.exch.z + P.anis1.z + P.anis2.z + P.zee.z + P.dmi.z);
 }
 
+// ----------------------------------------------------------------------------
+// spin-transfer torques (Sec. III), general stage kernels only
+// ----------------------------------------------------------------------------
+// Zhang-Li h = (u . grad) m at magnetic cell i of region r: central
+// differences; a missing neighbour (grid edge or vacuum) is the cell itself,
+// periodic axes wrap.
+__device__ __forceinline__ float3 zhang_li_h(const Geom& g, const Buffers& b, const Stt& S,
+                                             const float* __restrict__ m, int i, int x, int y, int z, int r,
+                                             float3 mi) {
+  const int sy = g.nx, sz = g.nx * g.ny, n = (int)g.n;
+  const int jp[3] = {x < g.nx - 1 ? i + 1 : (g.pbcx ? i - (g.nx - 1) : i),
+                     y < g.ny - 1 ? i + sy : (g.pbcy ? i - sy * (g.ny - 1) : i),
+                     z < g.nz - 1 ? i + sz : (g.pbcz ? i - sz * (g.nz - 1) : i)};
+  const int jm[3] = {x > 0 ? i - 1 : (g.pbcx ? i + g.nx - 1 : i),
+                     y > 0 ? i - sy : (g.pbcy ? i + sy * (g.ny - 1) : i),
+                     z > 0 ? i - sz : (g.pbcz ? i + sz * (g.nz - 1) : i)};
+  const float hd[3] = {S.hx, S.hy, S.hz};
+  float3 h = f3(0, 0, 0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int a1 = jp[a], a0 = jm[a];
+    const float3 v1 = b.code[a1] != kVacuum ? f3(m[a1], m[n + a1], m[2 * n + a1]) : mi;
+    const float3 v0 = b.code[a0] != kVacuum ? f3(m[a0], m[n + a0], m[2 * n + a0]) : mi;
+    const float c = __ldg(&S.lut->zlu[a][r]) * hd[a];
+    h.x += c * (v1.x - v0.x);
+    h.y += c * (v1.y - v0.y);
+    h.z += c * (v1.z - v0.z);
+  }
+  return h;
+}
+
+// Spin-transfer torques of region r at m, read in the sign convention of the
+// LL torque (dm/dt = -gamma tau): Zhang-Li -(a m x (m x h) + b m x h);
+// Slonczewski -g ((eps - al eps') m x (m_P x m) - (eps' - al eps) m x m_P),
+// g = gamma beta / (1 + al^2), eps = P L^2 / ((L^2 + 1) + (L^2 - 1) m.m_P).
+__device__ __forceinline__ float3 stt_torque(const Stt& S, int r, float3 m, float3 h) {
+  const SttLUT* __restrict__ L = S.lut;
+  float3 out = f3(0, 0, 0);
+  auto cr = [](float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+  };
+  if (S.zl) {
+    const float ca = __ldg(&L->zla[r]), cb = __ldg(&L->zlb[r]);
+    const float3 mh = cr(m, h), mmh = cr(m, mh);
+    out = f3(-(ca * mmh.x + cb * mh.x), -(ca * mmh.y + cb * mh.y), -(ca * mmh.z + cb * mh.z));
+  }
+  if (S.sl) {
+    const float3 mp = f3(__ldg(&L->mp[0][r]), __ldg(&L->mp[1][r]), __ldg(&L->mp[2][r]));
+    const float eps =
+        __ldg(&L->slp[r]) / (__ldg(&L->sl1[r]) + __ldg(&L->sl2[r]) * (m.x * mp.x + m.y * mp.y + m.z * mp.z));
+    const float ep = __ldg(&L->sle[r]), al = __ldg(&L->alpha[r]), gs = __ldg(&L->slg[r]);
+    const float t1 = gs * (eps - al * ep), t2 = gs * (ep - al * eps);
+    const float3 mpm = cr(mp, m), mmpm = cr(m, mpm), mmp = cr(m, mp);
+    out.x -= t1 * mmpm.x - t2 * mmp.x;
+    out.y -= t1 * mmpm.y - t2 * mmp.y;
+    out.z -= t1 * mmpm.z - t2 * mmp.z;
+  }
+  return out;
+}
+
+// LL torque plus the spin-transfer torques (if any) at magnetic cell i
+__device__ __forceinline__ float3 add_stt(const Geom& g, const Buffers& b, const Stt& S,
+                                          const float* __restrict__ m, int i, int x, int y, int z, int r, float3 mi,
+                                          float3 tq) {
+  if (!(S.zl || S.sl)) return tq;
+  const float3 h = S.zl ? zhang_li_h(g, b, S, m, i, x, y, z, r, mi) : f3(0, 0, 0);
+  const float3 ts = stt_torque(S, r, mi, h);
+  return f3(tq.x + ts.x, tq.y + ts.y, tq.z + ts.z);
+}
+
 
 __device__ __forceinline__ float3 llg_torque(float3 m, float3 B, float gfac, float alpha, int precession) {
   const float3 mxB = f3(m.y * B.z - m.z * B.y, m.z * B.x - m.x * B.z, m.x * B.y - m.y * B.x);

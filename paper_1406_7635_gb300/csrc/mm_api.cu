@@ -66,6 +66,9 @@ struct mm_ctx {
   double b0[kRegions][3]{}, b1[kRegions][3]{};
   double freq = 0, phase = 0;
   Terms T{1, 1, 1, 1, 0};
+  int stt_zl = 0, stt_sl = 0;   // switches of mm_enable_stt
+  Stt stt{};                     // active spin-transfer torques (set by flush_luts)
+  SttLUT* stt_lut = nullptr;     // device table
   int method = 0;                // host copy of DevState::method
   bool lut_dirty = true;
   bool m_set = false;
@@ -109,7 +112,8 @@ int flush_luts(mm_ctx* c) {
   RegionLUT L{};
   std::vector<float> X((size_t)kRegions * kXStride, 0.0f);
   double a[kRegions];
-  int dmi = 0;
+  int dmi = 0, zl = 0, sl = 0;
+  SttLUT SL{};
   for (int r = 0; r < kRegions; ++r) {
     const mm_material& m = c->mat[r];
     L.msat[r] = (float)m.msat;
@@ -128,6 +132,27 @@ int flush_luts(mm_ctx* c) {
     L.dmi[r] = m.msat > 0 ? (float)(2.0 * m.dind / m.msat) : 0.0f;
     L.dbc[r] = m.aex > 0 ? (float)(m.dind / (2.0 * m.aex)) : 0.0f;
     if (m.msat > 0 && m.dind != 0.0) dmi = 1;
+    // spin-transfer torques (Sec. III); constants in SI
+    const double muB = 9.2740100783e-24, qe = 1.602176634e-19, hbar = 1.054571817e-34;
+    const double a2 = 1.0 + m.alpha * m.alpha;
+    for (int k = 0; k < 3; ++k)
+      SL.zlu[k][r] = m.msat > 0 ? (float)(muB * m.jcur[k] / (2.0 * qe * m.msat * (1.0 + m.xi * m.xi))) : 0.0f;
+    SL.zla[r] = (float)((1.0 + m.xi * m.alpha) / a2);
+    SL.zlb[r] = (float)((m.xi - m.alpha) / a2);
+    const double beta = (m.msat > 0 && m.tfree > 0) ? m.jcur[2] * hbar / (m.msat * qe * m.tfree) : 0.0;
+    SL.slg[r] = (float)(m.gamma_ll * beta / a2);
+    const double l2 = m.lambda_sl * m.lambda_sl;
+    SL.slp[r] = (float)(m.pol * l2);
+    SL.sl1[r] = (float)(l2 + 1.0);
+    SL.sl2[r] = (float)(l2 - 1.0);
+    SL.sle[r] = (float)m.eps_prime;
+    SL.alpha[r] = (float)m.alpha;
+    const double np_ = std::sqrt(m.mp[0] * m.mp[0] + m.mp[1] * m.mp[1] + m.mp[2] * m.mp[2]);
+    for (int k = 0; k < 3; ++k) SL.mp[k][r] = np_ > 0 ? (float)(m.mp[k] / np_) : 0.0f;
+    if (m.msat > 0 && (m.jcur[0] != 0.0 || m.jcur[1] != 0.0 || m.jcur[2] != 0.0)) {
+      if (c->stt_zl) zl = 1;
+      if (c->stt_sl && m.tfree > 0 && m.jcur[2] != 0.0) sl = 1;
+    }
   }
   // 2 S(r1, r2) * harmonic mean of Aex/Msat (inter-region exchange)
   for (int r1 = 0; r1 < kRegions; ++r1)
@@ -138,15 +163,25 @@ int flush_luts(mm_ctx* c) {
     }
   MM_CUDA(cudaMemcpyAsync(c->b.lut, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
   MM_CUDA(cudaMemcpyAsync(c->b.xlut, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if (zl || sl) {
+    if (!c->stt_lut) MM_CUDA(cudaMalloc((void**)&c->stt_lut, sizeof(SttLUT)));
+    MM_CUDA(cudaMemcpyAsync(c->stt_lut, &SL, sizeof(SL), cudaMemcpyHostToDevice, c->stream));
+  }
   launch_codes(c->g, c->b, c->stream);
   MM_CUDA(cudaGetLastError());
   MM_CUDA(cudaStreamSynchronize(c->stream));
   c->lut_dirty = false;
-  if (dmi != c->T.dmi) {   // the DMI term and its boundary ghosts switch on or off
+  if (dmi != c->T.dmi || zl != c->stt.zl || sl != c->stt.sl) {   // terms switch on or off
     c->T.dmi = dmi;
+    c->stt.zl = zl;
+    c->stt.sl = sl;
     c->graph_valid = false;
     c->k1_valid = false;
   }
+  c->stt.lut = c->stt_lut;
+  c->stt.hx = (float)(0.5 / c->dx);
+  c->stt.hy = (float)(0.5 / c->dy);
+  c->stt.hz = (float)(0.5 / c->dz);
   return MM_OK;
 }
 
@@ -174,7 +209,10 @@ void enqueue_demag(mm_ctx* c) {
 // prep kernel, then per stage the (y, z) transform and one row kernel.
 // (a periodic x axis has no padding, so its rows do not fit the row
 // kernels' shared-memory stencil, which holds px / 2 cells per row)
-bool rowstage_path(const mm_ctx* c) { return c->g.fused && !c->sur_active && c->method == 0 && c->g.pbcx == 0; }
+// (the spin-transfer torques are evaluated by the general torque kernel only)
+bool rowstage_path(const mm_ctx* c) {
+  return c->g.fused && !c->sur_active && c->method == 0 && c->g.pbcx == 0 && !c->stt.zl && !c->stt.sl;
+}
 
 // stage-1 torque at the current m (FSAL start)
 void enqueue_k1(mm_ctx* c) {
@@ -188,7 +226,7 @@ void enqueue_k1(mm_ctx* c) {
   c->launches += 2 + (c->T.demag ? demag_launches(c->g) : 0);
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
   enqueue_demag(c);
-  launch_torque_t(c->g, c->b, c->T, 0, c->freq, c->phase, c->stream);
+  launch_torque_t(c->g, c->b, c->T, c->stt, 0, c->freq, c->phase, c->stream);
 }
 
 void enqueue_attempt(mm_ctx* c) {
@@ -208,7 +246,7 @@ void enqueue_attempt(mm_ctx* c) {
   for (int i = 0; i < ns; ++i) {
     launch_stage_input(c->g, c->b, slots[i], c->stream);
     enqueue_demag(c);
-    launch_torque_t(c->g, c->b, c->T, slots[i], c->freq, c->phase, c->stream);
+    launch_torque_t(c->g, c->b, c->T, c->stt, slots[i], c->freq, c->phase, c->stream);
   }
   launch_error_control(c->g, c->b, c->stream);
 }
@@ -288,7 +326,7 @@ int eval_field(mm_ctx* c, int mode) {
   if (mode == 3) return MM_OK;
   if (mode == 2 || mode == 4) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 9 * sizeof(double), c->stream));
   Terms T = c->T;
-  launch_field_out_t(c->g, c->b, T, c->b.ms, mode, c->freq, c->phase, c->stream);
+  launch_field_out_t(c->g, c->b, T, c->stt, c->b.ms, mode, c->freq, c->phase, c->stream);
   MM_CUDA(cudaGetLastError());
   return MM_OK;
 }
@@ -357,6 +395,8 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
     std::memset(&c->mat[r], 0, sizeof(mm_material));
     c->mat[r].gamma_ll = kGamma;
     c->mat[r].anis_u[0] = 1.0;
+    c->mat[r].lambda_sl = 1.0;
+    c->mat[r].mp[2] = 1.0;
   }
   c->S.assign((size_t)kRegions * kRegions, 1.0);
 
@@ -454,7 +494,7 @@ int mm_destroy(mm_ctx* c) {
   Buffers& b = c->b;
   void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.ms2, b.bd, b.out,
                   b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.code, b.st, b.hist, b.acc,
-                  b.fixed, c->sur_acc};
+                  b.fixed, c->sur_acc, c->stt_lut};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -738,6 +778,14 @@ int mm_get_energies(mm_ctx* c, mm_energies* out) {
   out->dmi = acc[8] * V;
   out->total = out->demag + out->exch + out->anis + out->zeeman + out->dmi;
   for (int k = 0; k < 3; ++k) out->m_avg[k] = acc[7] > 0 ? acc[4 + k] / acc[7] : 0.0;
+  return MM_OK;
+}
+
+int mm_enable_stt(mm_ctx* c, int zhang_li, int slonczewski) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  c->stt_zl = zhang_li != 0;
+  c->stt_sl = slonczewski != 0;
+  c->lut_dirty = true;   // the terms are switched on with the tables
   return MM_OK;
 }
 

@@ -30,6 +30,29 @@ struct RegionLUT {
   float dbc[kRegions];    // D / (2 Aex)              (boundary derivative; 0 if Aex = 0)
 };
 
+// Per-region spin-transfer-torque parameters (Sec. III, Zhang-Li and
+// Slonczewski torques), float32, derived on the host from mm_material.
+struct SttLUT {
+  float zlu[3][kRegions]; // Zhang-Li velocity mu_B j / (2 e Msat (1 + xi^2)) (m/s)
+  float zla[kRegions];    // (1 + xi alpha) / (1 + alpha^2)
+  float zlb[kRegions];    // (xi - alpha) / (1 + alpha^2)
+  float slg[kRegions];    // gamma beta / (1 + alpha^2), beta = j_z hbar / (Msat e d)
+  float slp[kRegions];    // P Lambda^2
+  float sl1[kRegions];    // Lambda^2 + 1
+  float sl2[kRegions];    // Lambda^2 - 1
+  float sle[kRegions];    // eps'
+  float mp[3][kRegions];  // fixed-layer direction
+  float alpha[kRegions];  // damping (the Slonczewski field-like mixing)
+};
+
+// Spin-transfer torques of a context: which are on, their table, and the
+// central-difference factors 1 / (2 Delta) of the Zhang-Li gradient.
+struct Stt {
+  int zl, sl;
+  const SttLUT* lut;
+  float hx, hy, hz;
+};
+
 // Grid and padded-FFT geometry.
 struct Geom {
   int nx, ny, nz;
@@ -159,14 +182,15 @@ void launch_begin_mode(const Buffers& b, int mode, long long nsteps, double t_en
 void launch_stage_input(const Geom& g, const Buffers& b, int stage, cudaStream_t s);
 // torque of stage `stage` (0..6) at m_s (stage 0: the current m), into the
 // k buffer holding that stage's role
-void launch_torque_t(const Geom& g, const Buffers& b, const Terms& T, int stage, double freq, double phase,
-                     cudaStream_t s);
+// (plus the spin-transfer torques S where switched on)
+void launch_torque_t(const Geom& g, const Buffers& b, const Terms& T, const Stt& S, int stage, double freq,
+                     double phase, cudaStream_t s);
 void launch_error_control(const Geom& g, const Buffers& b, cudaStream_t s);
 void launch_copy_mcur(const Geom& g, const Buffers& b, float* dst, cudaStream_t s);
 // getters at m, time st->t: mode 0 B_eff -> b.out, 1 torque -> b.out,
-// 2 energy sums -> b.acc
-void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const float* m, int mode, double freq,
-                        double phase, cudaStream_t s);
+// 2 energy sums -> b.acc, 4 max |torque| -> b.acc[0] (torques with S)
+void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const Stt& S, const float* m, int mode,
+                        double freq, double phase, cudaStream_t s);
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s);
 // cell codes from mask, region and the Msat table
 void launch_codes(const Geom& g, const Buffers& b, cudaStream_t s);

@@ -33,7 +33,9 @@ class MMError(RuntimeError):
 
 class mm_material(C.Structure):
     _fields_ = [("msat", C.c_double), ("aex", C.c_double), ("alpha", C.c_double), ("gamma_ll", C.c_double),
-                ("ku1", C.c_double), ("ku2", C.c_double), ("anis_u", C.c_double * 3), ("dind", C.c_double)]
+                ("ku1", C.c_double), ("ku2", C.c_double), ("anis_u", C.c_double * 3), ("dind", C.c_double),
+                ("jcur", C.c_double * 3), ("xi", C.c_double), ("pol", C.c_double), ("lambda_sl", C.c_double),
+                ("eps_prime", C.c_double), ("mp", C.c_double * 3), ("tfree", C.c_double)]
 
 
 class mm_energies(C.Structure):
@@ -88,6 +90,7 @@ _SIGS = {
     "mm_get_stats": (_I, [_P, C.POINTER(mm_stats)]),
     "mm_get_max_torque": (_I, [_P, C.POINTER(_D)]),
     "mm_set_pbc": (_I, [_P, _I, _I, _I]),
+    "mm_enable_stt": (_I, [_P, _I, _I]),
     "mm_set_integrator": (_I, [_P, _I]),
     "mm_get_integrator": (_I, [_P, C.POINTER(_I)]),
     "mm_relax": (_I, [_P, C.c_longlong, C.POINTER(C.c_longlong)]),
@@ -193,8 +196,10 @@ class Context:
         _check(mm_set_regions(self.h, None if a is None else _ptr(a)))
 
     def set_material(self, region, msat, aex, alpha, gamma_ll=1.7595e11, ku1=0.0, ku2=0.0, anis_u=(1.0, 0.0, 0.0),
-                     dind=0.0):
-        m = mm_material(msat, aex, alpha, gamma_ll, ku1, ku2, (C.c_double * 3)(*anis_u), dind)
+                     dind=0.0, jcur=(0.0, 0.0, 0.0), xi=0.0, pol=0.0, lambda_sl=1.0, eps_prime=0.0,
+                     mp=(0.0, 0.0, 1.0), tfree=0.0):
+        m = mm_material(msat, aex, alpha, gamma_ll, ku1, ku2, (C.c_double * 3)(*anis_u), dind,
+                        (C.c_double * 3)(*jcur), xi, pol, lambda_sl, eps_prime, (C.c_double * 3)(*mp), tfree)
         _check(mm_set_region_material(self.h, region, C.byref(m)))
 
     def set_exchange_scale(self, r1, r2, s):
@@ -269,6 +274,9 @@ class Context:
         _check(mm_get_energies(self.h, C.byref(e)))
         return {"total": e.total, "demag": e.demag, "exch": e.exch, "anis": e.anis, "zeeman": e.zeeman,
                 "dmi": e.dmi, "m_avg": list(e.m_avg)}
+
+    def enable_stt(self, zhang_li, slonczewski):
+        _check(mm_enable_stt(self.h, int(bool(zhang_li)), int(bool(slonczewski))))
 
     def set_pbc(self, px, py, pz):
         _check(mm_set_pbc(self.h, int(px), int(py), int(pz)))
@@ -350,7 +358,7 @@ class Context:
         for r in used:
             r = int(r)
             ctx.set_material(r, p.msat[r], p.aex[r], p.alpha[r], p.gamma[r], p.ku1[r], p.ku2[r], p.anis_u[r],
-                             p.dind[r])
+                             p.dind[r], p.jcur[r], p.xi[r], p.pol[r], p.lam[r], p.epsp[r], p.mp[r], p.tfree[r])
             ctx.set_bext(r, p.b0[r], p.b1[r])
         for i, r1 in enumerate(used):
             for r2 in used[i + 1:]:
@@ -359,6 +367,8 @@ class Context:
                     ctx.set_exchange_scale(int(r1), int(r2), s)
         ctx.set_bext_timefn(p.freq, p.phase)
         ctx.enable_terms(p.demag, p.exch, p.anis, p.zeeman, p.precession)
+        if p.zhang_li or p.slonczewski:
+            ctx.enable_stt(p.zhang_li, p.slonczewski)
         ctx.set_solver(p.max_err, p.headroom, p.dt0, p.dt_min, p.dt_max)
         ctx.set_m(p.m0)
         return ctx
