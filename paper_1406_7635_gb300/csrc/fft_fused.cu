@@ -210,6 +210,12 @@ __device__ __forceinline__ void kernel_mul(float2* s, const float* __restrict__ 
 // that three components and their kernel coefficients fit in registers)
 __host__ __device__ constexpr int zmid_radix(int lz) { return lz >= 4 ? 4 : lz; }
 
+// split cluster barrier: arrive without memory ordering, and the wait
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
+
 // The middle of the z transforms of all three components, fused (LZ =
 // R0 R1 with R1 = zmid_radix(LZ) the radix of the last forward pass, R0 = 1
 // for one pass):
@@ -456,8 +462,9 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
 // k_yz for clusters split in z (clz = 2): the y transform commutes with the
 // z-class twiddle (a per-row factor), so the two blocks of a z-class pair
 // (same ry) share it.  Each block loads and y-transforms one half of the z
-// rows (its half h = rz), takes the other half from its partner through
-// distributed shared memory, and after the inverse z pass sums the pair's
+// rows (its half h = rz) and stores it into its partner's shared memory
+// (distributed shared memory), which receives the other half the same way;
+// after the inverse z pass each block sums the pair's
 // two classes (conjugate z twiddle) for its half of the rows, so the inverse
 // y transform also runs on half the rows.  The last step adds the y classes
 // (cly = 2) as before.  Same shared-memory layout as k_yz.
@@ -484,11 +491,12 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   for (int i = threadIdx.x; i < LZ; i += NT) rtz[i] = __ldg(&tw[(i * (kTwN / g.pz)) & (kTwN - 1)]);
   const int CL = g.cly * 2;
   cg::cluster_group cluster = cg::this_cluster();
+  cluster_arrive_relaxed();   // "started": awaited before the first remote store
   const int rank = (int)cluster.block_rank();
   const int ry = rank % g.cly, rz = rank / g.cly;
   const int zpart = ry + g.cly * (1 - rz);   // same ry, other z class
   const int kx = (blockIdx.x / CL) % g.hx;
-  const int h0 = rz * H, ho = (1 - rz) * H;  // first row of my half, of the partner's half
+  const int h0 = rz * H;                     // first row of my half
   const int cstride = g.hx * g.nz * g.ny;
   float2* const plane = spec + kx * g.nz * g.ny;
   // 1. load my half of the rows
@@ -508,31 +516,20 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   // 2. forward y on my half of the rows of all three components (pencil q:
   //    component q / H, row h0 + q % H), y-class twiddle on load
   FftG<LY, -1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy, ry ? rty : nullptr);
-  // 3. the partner's half, transformed by the partner
-  cluster.sync();
+  // 3. my half into the partner's rows at the same positions, which the
+  //    partner neither loaded nor transformed (remote stores, no round trip)
+  cluster_wait();
   {
-    const float2* ps = cluster.map_shared_rank(s, zpart);
+    float2* pd = cluster.map_shared_rank(s, zpart);
     constexpr int NB = 3 * PH;
-    constexpr int PER = (NB + NT - 1) / NT;
-    float2 v[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * NT;
-      if (NB % NT == 0 || e < NB) {
-        const int y = e % LY, i = (e / LY) % H, c = e / PH;
-        v[q] = ps[c * CS + (ho + i) * RP + y];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * NT;
-      if (NB % NT == 0 || e < NB) {
-        const int y = e % LY, i = (e / LY) % H, c = e / PH;
-        s[c * CS + (ho + i) * RP + y] = v[q];
-      }
+#pragma unroll 4
+    for (int e = threadIdx.x; e < NB; e += NT) {
+      const int y = e % LY, i = (e / LY) % H, c = e / PH;
+      const int a = c * CS + (h0 + i) * RP + y;
+      pd[a] = s[a];
     }
   }
-  cluster.sync();   // the partner's rows are read before anyone transforms in z
+  cluster.sync();   // the pushed rows are complete before anyone transforms in z
   // 4. z: first pass (z-class twiddle on load), fused middle, last inverse pass
   constexpr int R0 = LZ / zmid_radix(LZ);
   if constexpr (R0 > 1) {
@@ -594,7 +591,10 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
       plane[c * cstride + z * g.ny + y] = v;
     }
   }
-  cluster.sync();   // keep shared memory alive until every peer has read it
+  // keep shared memory alive until every peer has read it (the reads have
+  // been consumed before each peer arrives, so no memory ordering is needed)
+  cluster_arrive_relaxed();
+  cluster_wait();
 }
 
 // rows per block of the x-row kernels: the default rule (enough blocks to

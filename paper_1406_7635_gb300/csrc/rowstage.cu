@@ -206,7 +206,57 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
   load_tables<L, NT>(twl, tw2, b.tw);
-  // 1. x C2R of the demag spectrum rows (3 components)
+  const int par = st->parity;
+  const float* __restrict__ m = par ? p.m1 : p.m0;
+  const int n = (int)g.n;
+  // 1. sums over the earlier stages at the block's cells, read from global
+  //    memory while the asynchronous copies are in flight: next stage
+  //    m + dt sum_j a_{s+1,j} k_j, or the error sum dt sum_j e_j k_j.  The
+  //    stage loop is unrolled (a zero coefficient skips its loads) so that all
+  //    loads of a cell are issued before the first is used.
+  float cj[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    cj[j] = mode == ROW_NEXT ? (j < s ? sc->ah[s + 1][j] : 0.f) : (mode == ROW_LAST ? sc->eh[j] : 0.f);
+  float av[CPT][3];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int e = threadIdx.x + q * NT;
+    av[q][0] = av[q][1] = av[q][2] = 0.f;
+    if (mode == ROW_K1 || e >= NCELL) continue;
+    const int x = e % L, r = e / L, y = y0 + r;
+    if (x >= g.nx || y >= g.ny) continue;
+    const int i = (z * g.ny + y) * g.nx + x;
+    float kj[6][3];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      kj[j][0] = kj[j][1] = kj[j][2] = 0.f;
+      if (cj[j] != 0.0f) {
+        const float* __restrict__ k = pick_k(p, k_role(j, par));
+        kj[j][0] = k[i];
+        kj[j][1] = k[n + i];
+        kj[j][2] = k[2 * n + i];
+      }
+    }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (mode == ROW_NEXT) {
+      a0 = m[i];
+      a1 = m[n + i];
+      a2 = m[2 * n + i];
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (cj[j] != 0.0f) {
+        a0 = fmaf(cj[j], kj[j][0], a0);
+        a1 = fmaf(cj[j], kj[j][1], a1);
+        a2 = fmaf(cj[j], kj[j][2], a2);
+      }
+    }
+    av[q][0] = a0;
+    av[q][1] = a1;
+    av[q][2] = a2;
+  }
+  // 2. x C2R of the demag spectrum rows (3 components)
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
   __syncthreads();
   for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
@@ -229,48 +279,6 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   }
   __syncthreads();
   FftG<L, 1, 3 * ROWS, NT, 1, PST, 1, L>::run(sm, twl);
-  const int par = st->parity;
-  const float* __restrict__ m = par ? p.m1 : p.m0;
-  const int n = (int)g.n;
-  // 2. sums over the earlier stages at the block's cells (global streams):
-  //    next stage m + dt sum_j a_{s+1,j} k_j, or the error sum dt sum_j e_j k_j
-  float av[CPT][3];
-#pragma unroll
-  for (int q = 0; q < CPT; ++q) {
-    const int e = threadIdx.x + q * NT;
-    av[q][0] = av[q][1] = av[q][2] = 0.f;
-    if (mode == ROW_K1 || e >= NCELL) continue;
-    const int x = e % L, r = e / L, y = y0 + r;
-    if (x >= g.nx || y >= g.ny) continue;
-    const int i = (z * g.ny + y) * g.nx + x;
-    if (mode == ROW_NEXT) {
-      float a0 = m[i], a1 = m[n + i], a2 = m[2 * n + i];
-      for (int j = 0; j < s; ++j) {
-        const float a = sc->ah[s + 1][j];
-        if (a == 0.0f) continue;
-        const float* __restrict__ k = pick_k(p, k_role(j, par));
-        a0 = fmaf(a, k[i], a0);
-        a1 = fmaf(a, k[n + i], a1);
-        a2 = fmaf(a, k[2 * n + i], a2);
-      }
-      av[q][0] = a0;
-      av[q][1] = a1;
-      av[q][2] = a2;
-    } else {
-      float ex = 0.f, ey = 0.f, ez = 0.f;
-      for (int j = 0; j < 6; ++j) {
-        const float c = sc->eh[j];
-        if (c == 0.0f) continue;
-        const float* __restrict__ k = pick_k(p, k_role(j, par));
-        ex = fmaf(c, k[i], ex);
-        ey = fmaf(c, k[n + i], ey);
-        ez = fmaf(c, k[2 * n + i], ez);
-      }
-      av[q][0] = ex;
-      av[q][1] = ey;
-      av[q][2] = ez;
-    }
-  }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   // 3. field and torque of the block's cells, stencil from shared memory
