@@ -243,4 +243,18 @@ __device__ __forceinline__ void load_twiddles(float2* dst, const float2* __restr
   for (int i = threadIdx.x; i < L; i += NT) dst[i] = __ldg(&tw[i * (kTwN / L)]);
 }
 
+// 8-byte asynchronous global -> shared copy (completes with the caller's
+// next cp.async.commit_group / wait)
+__device__ __forceinline__ void cp_async_f2(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// W_TWN^(i * stride mod TWN) for i < n, as asynchronous copies: the per-length
+// table (stride kTwN / L) or a residue-class twiddle (stride kTwN / P)
+template <int NT>
+__device__ __forceinline__ void twiddles_async(float2* dst, const float2* __restrict__ tw, int n, int stride) {
+  for (int i = threadIdx.x; i < n; i += NT) cp_async_f2(dst + i, tw + ((i * stride) & (kTwN - 1)));
+}
+
 }  // namespace mmfft

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
   __shared__ float2 s[ROWS * PST];
   __shared__ float2 twl[L], tw2[L + 1];   // W_L^i and W_2L^k
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z % 3;
-  load_twiddles<L, NT>(twl, tw);
-  for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
+  twiddles_async<NT>(twl, tw, L, kTwN / L);
+  twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
   const bool even = (g.nx & 1) == 0;
   const float* __restrict__ mc = m + c * (int)g.n;   // this component (3 n < 2^31)
   for (int e = threadIdx.x; e < ROWS * L; e += NT) {
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
     }
     s[r * PST + n] = v;
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   FftG<L, -1, ROWS, NT, 1, PST, 1, L>::run(s, twl);
   // X_k = E_k + W_P^k O_k; store with consecutive threads on consecutive y
@@ -114,12 +115,14 @@ __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ 
   __shared__ float2 s[ROWS * PST];
   __shared__ float2 twl[L], tw2[L + 1];   // W_L^i and W_2L^k
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z % 3;
-  load_twiddles<L, NT>(twl, tw);
-  for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
+  twiddles_async<NT>(twl, tw, L, kTwN / L);
+  twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
   for (int e = threadIdx.x; e < ROWS * (L + 1); e += NT) {
     const int r = e % ROWS, k = e / ROWS, y = y0 + r;
-    s[r * PST + k] = y < g.ny ? spec[tidx(g, c, k, z, y)] : make_float2(0.f, 0.f);
+    if (y < g.ny) cp_async_f2(&s[r * PST + k], spec + tidx(g, c, k, z, y));
+    else s[r * PST + k] = make_float2(0.f, 0.f);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   for (int e = threadIdx.x; e < ROWS * (L / 2 + 1); e += NT) {
     const int r = e / (L / 2 + 1), k = e % (L / 2 + 1);
@@ -354,11 +357,11 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   float2* twz = twy + LY;
   float2* rty = twz + LZ;
   float2* rtz = rty + LY;
-  load_twiddles<LY, NT>(twy, tw);
-  load_twiddles<LZ, NT>(twz, tw);
-  for (int i = threadIdx.x; i < LY; i += NT) rty[i] = __ldg(&tw[(i * (kTwN / g.py)) & (kTwN - 1)]);
-  for (int i = threadIdx.x; i < LZ; i += NT) rtz[i] = __ldg(&tw[(i * (kTwN / g.pz)) & (kTwN - 1)]);
-  __syncthreads();
+  // (asynchronous copies, completed with the plane's)
+  twiddles_async<NT>(twy, tw, LY, kTwN / LY);
+  twiddles_async<NT>(twz, tw, LZ, kTwN / LZ);
+  twiddles_async<NT>(rty, tw, LY, kTwN / g.py);
+  twiddles_async<NT>(rtz, tw, LZ, kTwN / g.pz);
   const int CL = g.cly * g.clz;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
@@ -485,10 +488,11 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   float2* twz = twy + LY;
   float2* rty = twz + LZ;
   float2* rtz = rty + LY;
-  load_twiddles<LY, NT>(twy, tw);
-  load_twiddles<LZ, NT>(twz, tw);
-  for (int i = threadIdx.x; i < LY; i += NT) rty[i] = __ldg(&tw[(i * (kTwN / g.py)) & (kTwN - 1)]);
-  for (int i = threadIdx.x; i < LZ; i += NT) rtz[i] = __ldg(&tw[(i * (kTwN / g.pz)) & (kTwN - 1)]);
+  // (asynchronous copies, completed with the plane's)
+  twiddles_async<NT>(twy, tw, LY, kTwN / LY);
+  twiddles_async<NT>(twz, tw, LZ, kTwN / LZ);
+  twiddles_async<NT>(rty, tw, LY, kTwN / g.py);
+  twiddles_async<NT>(rtz, tw, LZ, kTwN / g.pz);
   const int CL = g.cly * 2;
   cg::cluster_group cluster = cg::this_cluster();
   cluster_arrive_relaxed();   // "started": awaited before the first remote store

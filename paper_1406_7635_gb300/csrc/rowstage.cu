@@ -49,10 +49,12 @@ __device__ __forceinline__ void rows_fx(const Geom& g, float2* s, const float2* 
   }
 }
 
+// the x-transform tables W_L^i (i < L) and W_2L^k (k <= L), as asynchronous
+// copies (awaited with the caller's next cp.async wait)
 template <int L, int NT>
 __device__ __forceinline__ void load_tables(float2* twl, float2* tw2, const float2* __restrict__ tw) {
-  load_twiddles<L, NT>(twl, tw);
-  for (int k = threadIdx.x; k <= L; k += NT) tw2[k] = __ldg(&tw[k * (kTwN / (2 * L))]);
+  twiddles_async<NT>(twl, tw, L, kTwN / L);
+  twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
 }
 
 template <int L, int ROWS, int NT>
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   __shared__ float2 twl[L], tw2[L + 1];
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
   load_tables<L, NT>(twl, tw2, b.tw);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   float* sf = reinterpret_cast<float*>(sm);
   const int par = st->parity;
   const float* __restrict__ m = par ? p.m1 : p.m0;
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
     }
     for (int c = 0; c < 3; ++c) sf[2 * (c * ROWS + r) * PST + x] = v[c];
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
 }
@@ -193,9 +197,9 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   __shared__ float wmax[32];
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
   const float* __restrict__ ms = stage_buf(b, s);
-  // 0. asynchronous copies: the demag spectrum rows (first group), then the
-  //    stencil rows of the stage input (second group, awaited only after the
-  //    x transform)
+  // 0. asynchronous copies: the demag spectrum rows and the twiddle tables
+  //    (first group), then the stencil rows of the stage input (second group,
+  //    awaited only after the x transform)
   for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
     const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
     const int y = y0 + r;
@@ -203,9 +207,9 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     if (y < g.ny) cp_async8(dst, b.spec + tix(g, c, k, z, y));
     else *dst = make_float2(0.f, 0.f);
   }
+  load_tables<L, NT>(twl, tw2, b.tw);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
-  load_tables<L, NT>(twl, tw2, b.tw);
   const int par = st->parity;
   const float* __restrict__ m = par ? p.m1 : p.m0;
   const int n = (int)g.n;
