@@ -10,6 +10,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace mmfft {
 
 constexpr int kTwN = 2048;   // twiddle table length: largest supported L
@@ -236,6 +238,76 @@ struct FftW<L, DIR, NP, INNER, BS, ES, TWL, P, true> {
 // pencils stored as rows with pitch PST, twiddles from the global table
 template <int L, int DIR, int NP, int NT, int PST>
 using Fft = FftG<L, DIR, NP, NT, 1, PST, 1>;
+
+// A shared-memory pencil layout: element i of pencil p at
+// (p / INNER) * BS + (p % INNER) + i * ES.
+template <int INNER_, int BS_, int ES_>
+struct Lay {
+  static constexpr int INNER = INNER_, BS = BS_, ES = ES_;
+  __device__ __forceinline__ static int at(int p, int i) { return (p / INNER) * BS + (p % INNER) + i * ES; }
+};
+
+// A Stockham pass as stockham_pass, reading its inputs in layout LI and
+// writing its outputs in layout LO over the same buffer (every read of the
+// pass completes before the barrier, every write comes after it).
+template <int L, int R, int NS, int DIR, int NP, int NT, class LI, class LO, int TWL>
+__device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restrict__ tw) {
+  constexpr int NB = L / R;
+  constexpr int TOT = NB * NP;
+  constexpr int PER = (TOT + NT - 1) / NT;
+  float2 v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * NT;
+    if (TOT % NT == 0 || b < TOT) {
+      const int p = b % NP, j = b / NP;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = s[LI::at(p, j + r * NB)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * NT;
+    if (TOT % NT == 0 || b < TOT) {
+      const int p = b % NP, j = b / NP;
+      const int k = j % NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[(r * k * (TWL / (NS * R))) & (TWL - 1)];
+          if (DIR > 0) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      Dft<R, DIR>::run(v[q]);
+      const int o = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[LO::at(p, o + r * NS)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full length-L transform of NP pencils whose first pass reads layout LI,
+// whose last pass writes layout LO and whose other passes use layout LM.
+// Callers synchronise before; ends with __syncthreads().
+template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P = 0,
+          bool DONE = (P >= npasses(L))>
+struct FftX;
+template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P>
+struct FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P, false> {
+  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw) {
+    using In = typename std::conditional<P == 0, LI, LM>::type;
+    using Out = typename std::conditional<P + 1 == npasses(L), LO, LM>::type;
+    stockham_pass_x<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, In, Out, TWL>(s, tw);
+    FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P + 1>::run(s, tw);
+  }
+};
+template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P>
+struct FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P, true> {
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__) {}
+};
 
 // copy W_L^i (i < L) out of the global 2048-entry table into shared memory
 template <int L, int NT>

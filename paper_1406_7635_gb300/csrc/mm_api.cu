@@ -68,6 +68,7 @@ struct mm_ctx {
   Terms T{1, 1, 1, 1, 0};
   int stt_zl = 0, stt_sl = 0;   // switches of mm_enable_stt
   Stt stt{};                     // active spin-transfer torques (set by flush_luts)
+  RsMaps maps{};                 // tensor maps of the row-stage kernels (rowstage_maps)
   SttLUT* stt_lut = nullptr;     // device table
   int method = 0;                // host copy of DevState::method
   bool lut_dirty = true;
@@ -218,9 +219,9 @@ bool rowstage_path(const mm_ctx* c) {
 void enqueue_k1(mm_ctx* c) {
   if (rowstage_path(c)) {
     c->launches += 2 + (c->T.demag ? 1 : 0);
-    launch_rowstage(c->g, c->b, c->T, 0, 0, 0, c->freq, c->phase, c->stream);
+    launch_rowstage(c->g, c->b, c->T, c->maps, 0, 0, 0, c->freq, c->phase, c->stream);
     if (c->T.demag) launch_demag_yz(c->g, c->b, c->stream);
-    launch_rowstage(c->g, c->b, c->T, 1, 0, 0, c->freq, c->phase, c->stream);
+    launch_rowstage(c->g, c->b, c->T, c->maps, 1, 0, 0, c->freq, c->phase, c->stream);
     return;
   }
   c->launches += 2 + (c->T.demag ? demag_launches(c->g) : 0);
@@ -231,10 +232,10 @@ void enqueue_k1(mm_ctx* c) {
 
 void enqueue_attempt(mm_ctx* c) {
   if (rowstage_path(c)) {
-    launch_rowstage(c->g, c->b, c->T, 0, 1, 0, c->freq, c->phase, c->stream);
+    launch_rowstage(c->g, c->b, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
     for (int s = 1; s < 7; ++s) {
       if (c->T.demag) launch_demag_yz(c->g, c->b, c->stream);
-      launch_rowstage(c->g, c->b, c->T, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
+      launch_rowstage(c->g, c->b, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
     }
     return;
   }
@@ -481,6 +482,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && g.fused) e = prepare_rowstage(g);
+  if (e == cudaSuccess) rowstage_maps(g, b, &c->maps);
   if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, std::string("warm-up: ") + cudaGetErrorString(e)));
   *out = c;
   return MM_OK;
@@ -832,6 +834,7 @@ int mm_set_pbc(mm_ctx* c, int px, int py, int pz) {
     if (e == cudaSuccess) e = cudaGetLastError();
   }
   if (e == cudaSuccess && g.fused && g.pbcx == 0) e = prepare_rowstage(g);
+  if (e == cudaSuccess) rowstage_maps(g, b, &c->maps);
   if (e != cudaSuccess)
     return fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,
                 std::string("set_pbc: ") + cudaGetErrorString(e));

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -157,11 +158,27 @@ void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, c
 void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s);
 // only the (y, z) part of the fused convolution (k_yz), spectrum in place
 void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s);
+// Tensor maps of the row-stage kernels' TMA path (rowstage.cu): the spectrum
+// [3][hx][nz][ny] (8-byte elements) with box (ROWS, 1, L + 1, 3), the stage
+// inputs [3][nz][ny][nx] with boxes (L, ROWS + 2, 1, 1) (own plane and the
+// two halo rows) and (L, ROWS, 1, 1) (neighbour planes), and the cell codes
+// [nz][ny][nx] with the same two boxes.  ok = 0: the grid takes the cp.async
+// path.
+struct RsMaps {
+  CUtensorMap spec;
+  CUtensorMap ms_own, ms_pl, ms2_own, ms2_pl;
+  CUtensorMap code_own, code_pl;
+  int ok;
+};
+// fills *m for this grid and its buffers (m->ok = 0 when the TMA path does
+// not apply or the driver's encoder is unavailable)
+void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m);
+
 // fused RK45 stage kernels (rowstage.cu): kind 0 = stage-input prep of stage
 // s, kind 1 = row kernel of stage s (mode 0 first stage only, 1 next stage,
-// 2 last stage with error and controller)
-void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
-                     double phase, cudaStream_t st);
+// 2 last stage with error and controller); maps from rowstage_maps
+void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
+                     double freq, double phase, cudaStream_t st);
 // kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
                                   cudaStream_t s);

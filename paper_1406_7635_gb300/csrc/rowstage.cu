@@ -13,6 +13,8 @@
 //              block) the step controller (Sec. IV).
 // Stage inputs alternate between two buffers (ms for even stages, ms2 for odd
 // ones), because a stage's stencil reads neighbours owned by other blocks.
+#include <cstring>
+
 #include "fft.cuh"
 #include "llg_device.cuh"
 
@@ -49,6 +51,108 @@ __device__ __forceinline__ void rows_fx(const Geom& g, float2* s, const float2* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) path: the spectrum box of a block is one tensor
+// copy each way, the stencil rows twelve; completion through mbarriers that a
+// single thread waits on with a time limit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Waits for phase 0 of bar to complete; false after about 2^30 cycles
+// (half a second), so that a lost transfer ends the kernel with an error
+// instead of a hang.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar))
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 30)) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3, const void* src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(map),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// the block's own bulk stores have finished reading shared memory (the
+// global writes complete with the grid, before the next kernel in the stream)
+__device__ __forceinline__ void tma_store_drain() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the tensor copies
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Pencil layouts of the block's spectrum rows: the tensor box [c][k][r]
+// (A: element k of pencil (c, r) at (c (L + 1) + k) ROWS + r) and rows of
+// pitch L + 1 (B, the layout the field code reads and the stage input is
+// written in).
+template <int L, int ROWS>
+using LayA = Lay<ROWS, (L + 1) * ROWS, ROWS>;
+template <int L>
+using LayB = Lay<1, L + 1, 1>;
+
+// x R2C of the packed rows in s (layout B) into the spectrum by one tensor
+// store: the first pass moves the rows into the box layout A, the post-pass
+// X_k = E_k + W_2L^k O_k runs on the pairs (k, L - k) in place (X_L beside),
+// rows past the grid are clipped by the store.
+template <int L, int ROWS, int NT>
+__device__ __forceinline__ void rows_fx_tma(float2* s, const float2* twl, const float2* tw2, const CUtensorMap* map,
+                                            int y0, int z) {
+  using A = LayA<L, ROWS>;
+  FftX<L, -1, 3 * ROWS, NT, LayB<L>, A, A, L>::run(s, twl);
+  for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
+    const int pen = e % (3 * ROWS), k = e / (3 * ROWS);
+    const int ia = A::at(pen, k), ib = A::at(pen, (L - k) & (L - 1));
+    const float2 zk = s[ia], zl = s[ib];
+    {
+      const float2 zc = cconj(zl);
+      const float2 E = cscale(cadd(zk, zc), 0.5f);
+      const float2 d = csub(zk, zc);
+      s[ia] = cadd(E, cmul(tw2[k], make_float2(0.5f * d.y, -0.5f * d.x)));
+    }
+    {
+      const float2 zc = cconj(zk);
+      const float2 E = cscale(cadd(zl, zc), 0.5f);
+      const float2 d = csub(zl, zc);
+      const float2 X = cadd(E, cmul(tw2[L - k], make_float2(0.5f * d.y, -0.5f * d.x)));
+      if (k == 0) s[A::at(pen, L)] = X;
+      else if (k != L / 2) s[ib] = X;
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma_store_4d(map, y0, z, 0, 0, s);
+    tma_store_drain();
+  }
+}
+
 // the x-transform tables W_L^i (i < L) and W_2L^k (k <= L), as asynchronous
 // copies (awaited with the caller's next cp.async wait)
 template <int L, int NT>
@@ -57,12 +161,13 @@ __device__ __forceinline__ void load_tables(float2* twl, float2* tw2, const floa
   twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
 }
 
-template <int L, int ROWS, int NT>
+template <int L, int ROWS, int NT, bool TS>
 __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const DevState* __restrict__ st,
-                                               const StageCoef* __restrict__ sc, int s) {
+                                               const StageCoef* __restrict__ sc, int s,
+                                               const __grid_constant__ RsMaps maps) {
   if (st->done) return;
   constexpr int PST = L + 1;
-  __shared__ float2 sm[3 * ROWS * PST];
+  __shared__ __align__(128) float2 sm[3 * ROWS * PST];
   __shared__ float2 twl[L], tw2[L + 1];
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
   load_tables<L, NT>(twl, tw2, b.tw);
@@ -98,7 +203,8 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
+  if constexpr (TS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
+  else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
 }
 
 // Shared-memory layout of the row kernel (dynamic): the demag rows of the
@@ -110,11 +216,24 @@ template <int L, int ROWS>
 struct RsSmem {
   static constexpr int PST = L + 1;
   static constexpr int NR = 3 * ROWS + 2;
-  static constexpr int SPEC = ((3 * ROWS * PST * 8) + 15) / 16 * 16;
+  static constexpr int SPEC = ((3 * ROWS * PST * 8) + 127) / 128 * 128;
   static constexpr int STEN = 3 * NR * L * 4;
   static constexpr int CODE = NR * L * 4;
-  static constexpr int BYTES = SPEC + STEN + CODE;
+  // (+128: the base is rounded up to 128 bytes, the alignment of tensor copies)
+  static constexpr int BYTES = SPEC + STEN + CODE + 128;
 };
+
+// Which copies of the row kernels go through the tensor engine where the
+// shape allows it: the spectrum box (load and store) and the stencil rows.
+constexpr bool kRsTS = true;
+constexpr bool kRsTT = true;
+
+// The row kernels take the TMA path for lengths 32..128 with at least 8 rows
+// per block (row starts 128-byte aligned, conflict-free box layout).
+template <int L, int ROWS>
+constexpr bool rs_tma_shape() {
+  return L >= 32 && L <= 128 && ROWS >= 8;
+}
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -178,10 +297,12 @@ __device__ __forceinline__ void stage_stencil(const Geom& g, const float* __rest
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-template <int L, int ROWS, int NT>
+// TS: the spectrum rows by tensor copies (load and store), TT: the stencil
+// rows by tensor copies; otherwise asynchronous copies and plain stores
+template <int L, int ROWS, int NT, bool TS, bool TT>
 __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Ptrs p, DevState* __restrict__ st,
                                                  StageCoef* __restrict__ sc, int s, int mode, double freq,
-                                                 double phase_over_pi) {
+                                                 double phase_over_pi, const __grid_constant__ RsMaps maps) {
   if (st->done) return;   // uniform: the controller runs after every block of this launch
   using SM = RsSmem<L, ROWS>;
   constexpr int PST = SM::PST, NR = SM::NR;
@@ -190,26 +311,62 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   constexpr int CPT = (ROWS * L + NT - 1) / NT;
   constexpr int NCELL = ROWS * L;   // cell slots: x < L of each row (x >= nx idle)
   extern __shared__ float4 rs_dyn[];
-  float2* sm = reinterpret_cast<float2*>(rs_dyn);
-  float* sten = reinterpret_cast<float*>(reinterpret_cast<char*>(rs_dyn) + SM::SPEC);
-  int* scode = reinterpret_cast<int*>(reinterpret_cast<char*>(rs_dyn) + SM::SPEC + SM::STEN);
+  char* const base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(rs_dyn) + 127) & ~uintptr_t(127));
+  float2* sm = reinterpret_cast<float2*>(base);
+  float* sten = reinterpret_cast<float*>(base + SM::SPEC);
+  int* scode = reinterpret_cast<int*>(base + SM::SPEC + SM::STEN);
   __shared__ float2 twl[L], tw2[L + 1];
   __shared__ float wmax[32];
+  __shared__ __align__(8) unsigned long long bars[2];   // TMA: spectrum, stencil
+  __shared__ int tma_ok;
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y;
   const float* __restrict__ ms = stage_buf(b, s);
-  // 0. asynchronous copies: the demag spectrum rows and the twiddle tables
-  //    (first group), then the stencil rows of the stage input (second group,
-  //    awaited only after the x transform)
-  for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
-    const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
-    const int y = y0 + r;
-    float2* dst = sm + (c * ROWS + r) * PST + k;
-    if (y < g.ny) cp_async8(dst, b.spec + tix(g, c, k, z, y));
-    else *dst = make_float2(0.f, 0.f);
+  // 0. copies in flight: the demag spectrum rows and the twiddle tables, then
+  //    the stencil rows of the stage input (awaited only after the x
+  //    transform).  Tensor copies are issued by thread 0: the spectrum box
+  //    (layout A) and twelve boxes of stencil rows.
+  if constexpr (TS || TT) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0]);
+      mbar_init(&bars[1]);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if constexpr (TS) {
+        mbar_expect_tx(&bars[0], 3 * (L + 1) * ROWS * 8);
+        tma_load_4d(sm, &maps.spec, y0, z, 0, 0, &bars[0]);
+      }
+      if constexpr (TT) {
+        mbar_expect_tx(&bars[1], 16 * NR * L);
+        const CUtensorMap* own = (s & 1) ? &maps.ms2_own : &maps.ms_own;
+        const CUtensorMap* pl = (s & 1) ? &maps.ms2_pl : &maps.ms_pl;
+        // neighbour planes: wrapped on a periodic z, else out of range (zero
+        // filled, never read)
+        const int zm = g.pbcz ? (z + g.nz - 1) % g.nz : z - 1, zp = g.pbcz ? (z + 1) % g.nz : z + 1;
+        for (int c = 0; c < 3; ++c) {
+          tma_load_4d(sten + (c * NR) * L, own, 0, y0 - 1, z, c, &bars[1]);
+          tma_load_4d(sten + (c * NR + ROWS + 2) * L, pl, 0, y0, zm, c, &bars[1]);
+          tma_load_4d(sten + (c * NR + 2 * ROWS + 2) * L, pl, 0, y0, zp, c, &bars[1]);
+        }
+        tma_load_3d(scode, &maps.code_own, 0, y0 - 1, z, &bars[1]);
+        tma_load_3d(scode + (ROWS + 2) * L, &maps.code_pl, 0, y0, zm, &bars[1]);
+        tma_load_3d(scode + (2 * ROWS + 2) * L, &maps.code_pl, 0, y0, zp, &bars[1]);
+      }
+    }
+  }
+  if constexpr (!TS) {
+    for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
+      const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
+      const int y = y0 + r;
+      float2* dst = sm + (c * ROWS + r) * PST + k;
+      if (y < g.ny) cp_async8(dst, b.spec + tix(g, c, k, z, y));
+      else *dst = make_float2(0.f, 0.f);
+    }
   }
   load_tables<L, NT>(twl, tw2, b.tw);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
-  stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
+  if constexpr (!TT) stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
   const int par = st->parity;
   const float* __restrict__ m = par ? p.m1 : p.m0;
   const int n = (int)g.n;
@@ -260,13 +417,33 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     av[q][1] = a1;
     av[q][2] = a2;
   }
-  // 2. x C2R of the demag spectrum rows (3 components)
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-  __syncthreads();
+  // 2. x C2R of the demag spectrum rows (3 components); the output is in
+  //    rows of pitch L + 1 (layout B) on both paths
+  using A = LayA<L, ROWS>;
+  using Bl = LayB<L>;
+  using LIn = typename std::conditional<TS, A, Bl>::type;
+  if constexpr (TT) asm volatile("cp.async.wait_all;\n" ::: "memory");
+  else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  if constexpr (TS) {
+    if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[0]);
+    __syncthreads();
+    if (!tma_ok) {   // uniform; the copies in flight land before the block ends
+      if (threadIdx.x == 0) {
+        st->status = -6;   // MM_ERR_TIMEOUT
+        st->done = 1;
+        mbar_wait(&bars[0]);
+        if (TT) mbar_wait(&bars[1]);
+      }
+      return;
+    }
+  } else {
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
-    const int pen = e / (L / 2 + 1), k = e % (L / 2 + 1);
-    float2* row = sm + pen * PST;
-    const float2 xa = row[k], xb = row[L - k];
+    // (consecutive threads on consecutive pencils in layout A)
+    const int pen = TS ? e % (3 * ROWS) : e / (L / 2 + 1), k = TS ? e / (3 * ROWS) : e % (L / 2 + 1);
+    const int ia = LIn::at(pen, k), ib = LIn::at(pen, L - k);
+    const float2 xa = sm[ia], xb = sm[ib];
     float2 za, zb;
     {
       const float2 E = cscale(cadd(xa, cconj(xb)), 0.5f);
@@ -278,13 +455,26 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       const float2 O = cmul(cscale(csub(xb, cconj(xa)), 0.5f), cconj(tw2[L - k]));
       zb = make_float2(E.x - O.y, E.y + O.x);
     }
-    row[k] = za;
-    if (k != 0 && k != L / 2) row[L - k] = zb;
+    sm[ia] = za;
+    if (k != 0 && k != L / 2) sm[ib] = zb;
   }
   __syncthreads();
-  FftG<L, 1, 3 * ROWS, NT, 1, PST, 1, L>::run(sm, twl);
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
+  FftX<L, 1, 3 * ROWS, NT, LIn, LIn, Bl, L>::run(sm, twl);
+  if constexpr (TT) {
+    if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[1]);
+    __syncthreads();
+    if (!tma_ok) {
+      if (threadIdx.x == 0) {
+        st->status = -6;   // MM_ERR_TIMEOUT
+        st->done = 1;
+        mbar_wait(&bars[1]);
+      }
+      return;
+    }
+  } else {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+  }
   // 3. field and torque of the block's cells, stencil from shared memory
   const float* sf = reinterpret_cast<const float*>(sm);
   const RegionLUT* __restrict__ lut = b.lut;
@@ -405,7 +595,8 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       sw[2 * (2 * ROWS + r) * PST + x] = msat * n2;
     }
     __syncthreads();
-    rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
+    if constexpr (TS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
+    else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
     return;
   }
   // 4'. last stage: error estimate, candidate m, block max, controller
@@ -469,22 +660,41 @@ struct RsCfg {
 };
 
 template <int L, int ROWS>
-void launch_rs(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq, double phase,
-               cudaStream_t st) {
+void launch_rs(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
+               double freq, double phase, cudaStream_t st) {
   using C = RsCfg<L, ROWS>;
   dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz);
   StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
+  const double ph = phase / 3.14159265358979323846;
+  constexpr int SB = RsSmem<L, ROWS>::BYTES;
+  if constexpr (rs_tma_shape<L, ROWS>()) {
+    if (maps.ok) {
+      if (kind == 0)
+        k_rs_prep<L, ROWS, C::NT, kRsTS><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s, maps);
+      else
+        k_rs_row<L, ROWS, C::NT, kRsTS, kRsTT><<<grid, C::NT, SB, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq,
+                                                                        ph, maps);
+      return;
+    }
+  }
   if (kind == 0)
-    k_rs_prep<L, ROWS, C::NT><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s);
+    k_rs_prep<L, ROWS, C::NT, false><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s, maps);
   else
-    k_rs_row<L, ROWS, C::NT><<<grid, C::NT, RsSmem<L, ROWS>::BYTES, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode,
-                                                                          freq, phase / 3.14159265358979323846);
+    k_rs_row<L, ROWS, C::NT, false, false><<<grid, C::NT, SB, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq, ph,
+                                                                    maps);
 }
 
 template <int L, int ROWS>
 cudaError_t prepare_rs() {
-  return cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              RsSmem<L, ROWS>::BYTES);
+  constexpr int SB = RsSmem<L, ROWS>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT, false, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SB);
+  if constexpr (rs_tma_shape<L, ROWS>()) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT, kRsTS, kRsTT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, SB);
+  }
+  return e;
 }
 
 template <int L>
@@ -492,18 +702,63 @@ struct RsRows {
   static constexpr int R1 = L >= 1024 ? 1 : 1024 / L;
   static constexpr int R2 = L >= 256 ? 1 : 256 / L;
   static bool big(const Geom& g) { return (long long)((g.ny + R1 - 1) / R1) * g.nz >= 300; }
+  static int rows(const Geom& g) { return big(g) ? R1 : R2; }
 };
 
 template <int L>
-void launch_rs_l(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
-                 double phase, cudaStream_t st) {
-  if (RsRows<L>::big(g)) launch_rs<L, RsRows<L>::R1>(g, b, T, kind, s, mode, freq, phase, st);
-  else launch_rs<L, RsRows<L>::R2>(g, b, T, kind, s, mode, freq, phase, st);
+void launch_rs_l(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
+                 double freq, double phase, cudaStream_t st) {
+  if (RsRows<L>::big(g)) launch_rs<L, RsRows<L>::R1>(g, b, T, maps, kind, s, mode, freq, phase, st);
+  else launch_rs<L, RsRows<L>::R2>(g, b, T, maps, kind, s, mode, freq, phase, st);
 }
 
 template <int L>
 cudaError_t prepare_rs_l(const Geom& g) {
   return RsRows<L>::big(g) ? prepare_rs<L, RsRows<L>::R1>() : prepare_rs<L, RsRows<L>::R2>();
+}
+
+// rows per block of the row kernels for this grid
+int rs_rows(const Geom& g) {
+  switch (g.lx) {
+    case 16: return RsRows<16>::rows(g);
+    case 32: return RsRows<32>::rows(g);
+    case 64: return RsRows<64>::rows(g);
+    case 128: return RsRows<128>::rows(g);
+    case 256: return RsRows<256>::rows(g);
+    case 512: return RsRows<512>::rows(g);
+    default: return 0;
+  }
+}
+
+// the driver's tensor-map encoder, fetched once through the runtime (no link
+// against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+// one tiled map of `rank` dimensions (innermost first); strides in bytes of
+// dimensions 1..rank-1; zero fill out of range
+bool encode(CUtensorMap* m, CUtensorMapDataType t, int rank, void* base, const cuuint64_t* dims,
+            const cuuint64_t* strides, const cuuint32_t* box) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(m, t, (cuuint32_t)rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -520,17 +775,53 @@ cudaError_t prepare_rowstage(const Geom& g) {
   }
 }
 
+// TMA path conditions: a row-kernel shape with rs_tma_shape (32 <= L <= 128,
+// >= 8 rows per block), row strides of nx floats and ny complex values that
+// are multiples of 16 bytes, and no periodic y (the halo rows would wrap).
+void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m) {
+  std::memset(m, 0, sizeof(RsMaps));
+  const int L = g.lx, rows = rs_rows(g);
+  if (!g.fused || L < 32 || L > 128 || rows < 8 || g.nx % 4 != 0 || g.ny % 2 != 0 || g.pbcy || g.pbcx) return;
+  if (!b.spec || !b.ms || !b.ms2 || !b.code) return;
+  bool ok = true;
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)g.hx, 3};
+    const cuuint64_t st[3] = {(cuuint64_t)g.ny * 8, (cuuint64_t)g.nz * g.ny * 8, (cuuint64_t)g.hx * g.nz * g.ny * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)rows, 1, (cuuint32_t)(L + 1), 3};
+    ok = ok && encode(&m->spec, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, b.spec, dims, st, box);
+  }
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    const cuuint64_t st[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.ny * g.nx * 4, (cuuint64_t)g.n * 4};
+    const cuuint32_t own[4] = {(cuuint32_t)L, (cuuint32_t)(rows + 2), 1, 1};
+    const cuuint32_t pl[4] = {(cuuint32_t)L, (cuuint32_t)rows, 1, 1};
+    ok = ok && encode(&m->ms_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms, dims, st, own);
+    ok = ok && encode(&m->ms_pl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms, dims, st, pl);
+    ok = ok && encode(&m->ms2_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms2, dims, st, own);
+    ok = ok && encode(&m->ms2_pl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms2, dims, st, pl);
+  }
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t st[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.ny * g.nx * 4};
+    const cuuint32_t own[3] = {(cuuint32_t)L, (cuuint32_t)(rows + 2), 1};
+    const cuuint32_t pl[3] = {(cuuint32_t)L, (cuuint32_t)rows, 1};
+    ok = ok && encode(&m->code_own, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, b.code, dims, st, own);
+    ok = ok && encode(&m->code_pl, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, b.code, dims, st, pl);
+  }
+  m->ok = ok ? 1 : 0;
+}
+
 // kind 0: prep of stage s; kind 1: row kernel of stage s with mode 0 (first
 // stage only), 1 (next stage), 2 (last stage: error and controller)
-void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, int kind, int s, int mode, double freq,
-                     double phase, cudaStream_t st) {
+void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
+                     double freq, double phase, cudaStream_t st) {
   switch (g.lx) {
-    case 16: launch_rs_l<16>(g, b, T, kind, s, mode, freq, phase, st); break;
-    case 32: launch_rs_l<32>(g, b, T, kind, s, mode, freq, phase, st); break;
-    case 64: launch_rs_l<64>(g, b, T, kind, s, mode, freq, phase, st); break;
-    case 128: launch_rs_l<128>(g, b, T, kind, s, mode, freq, phase, st); break;
-    case 256: launch_rs_l<256>(g, b, T, kind, s, mode, freq, phase, st); break;
-    case 512: launch_rs_l<512>(g, b, T, kind, s, mode, freq, phase, st); break;
+    case 16: launch_rs_l<16>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
+    case 32: launch_rs_l<32>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
+    case 64: launch_rs_l<64>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
+    case 128: launch_rs_l<128>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
+    case 256: launch_rs_l<256>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
+    case 512: launch_rs_l<512>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
     default: break;
   }
 }
