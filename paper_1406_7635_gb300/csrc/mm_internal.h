@@ -162,15 +162,15 @@ void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s);
 // [3][hx][nz][ny] (8-byte elements) with box (ROWS, 1, L + 1, 3), the stage
 // inputs [3][nz][ny][nx] with boxes (L, ROWS + 2, 1, 1) (own plane and the
 // two halo rows) and (L, ROWS, 1, 1) (neighbour planes), and the cell codes
-// [nz][ny][nx] with the same two boxes.  ok = 0: the grid takes the cp.async
-// path.
+// [nz][ny][nx] with the same two boxes.  ok_spec / ok_sten = 0: the spectrum
+// / stencil rows take the cp.async path.
 struct RsMaps {
   CUtensorMap spec;
   CUtensorMap ms_own, ms_pl, ms2_own, ms2_pl;
   CUtensorMap code_own, code_pl;
-  int ok;
+  int ok_spec, ok_sten;
 };
-// fills *m for this grid and its buffers (m->ok = 0 when the TMA path does
+// fills *m for this grid and its buffers (a flag stays 0 when its copies do
 // not apply or the driver's encoder is unavailable)
 void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m);
 

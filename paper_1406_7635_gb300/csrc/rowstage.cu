@@ -161,7 +161,7 @@ __device__ __forceinline__ void load_tables(float2* twl, float2* tw2, const floa
   twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
 }
 
-template <int L, int ROWS, int NT, bool TS>
+template <int L, int ROWS, int NT, bool SS>
 __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const DevState* __restrict__ st,
                                                const StageCoef* __restrict__ sc, int s,
                                                const __grid_constant__ RsMaps maps) {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  if constexpr (TS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
+  if constexpr (SS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
   else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
 }
 
@@ -223,16 +223,27 @@ struct RsSmem {
   static constexpr int BYTES = SPEC + STEN + CODE + 128;
 };
 
-// Which copies of the row kernels go through the tensor engine where the
-// shape allows it: the spectrum box (load and store) and the stencil rows.
-constexpr bool kRsTS = true;
+// Which copies go through the tensor engine where the shape allows it: the
+// row kernel's spectrum box load (SL) and store (SS), its stencil rows (TT),
+// and the prep kernel's spectrum store (PS).  Measured on the 128 x 128 x 32
+// step (same GPU, ms per step): all four 0.5516, PS off 0.5472, SS and PS off
+// 0.5485, TT off 0.5643; the prep kernel's blocks are short and waiting for
+// their store to drain costs more than the scattered stores.
+constexpr bool kRsSL = true;
+constexpr bool kRsSS = true;
 constexpr bool kRsTT = true;
+constexpr bool kRsPS = false;
 
-// The row kernels take the TMA path for lengths 32..128 with at least 8 rows
-// per block (row starts 128-byte aligned, conflict-free box layout).
+// Spectrum boxes: rows of 32..128 complex values with at least 8 rows per
+// block (box dimension L + 1 <= 256, conflict-free box layout A).
 template <int L, int ROWS>
-constexpr bool rs_tma_shape() {
+constexpr bool rs_spec_shape() {
   return L >= 32 && L <= 128 && ROWS >= 8;
+}
+// Stencil rows: 32..256 floats (row starts 128-byte aligned, box <= 256).
+template <int L>
+constexpr bool rs_sten_shape() {
+  return L >= 32 && L <= 256;
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -297,9 +308,9 @@ __device__ __forceinline__ void stage_stencil(const Geom& g, const float* __rest
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// TS: the spectrum rows by tensor copies (load and store), TT: the stencil
+// SL / SS: the spectrum box loaded / stored by tensor copies, TT: the stencil
 // rows by tensor copies; otherwise asynchronous copies and plain stores
-template <int L, int ROWS, int NT, bool TS, bool TT>
+template <int L, int ROWS, int NT, bool SL, bool SS, bool TT>
 __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Ptrs p, DevState* __restrict__ st,
                                                  StageCoef* __restrict__ sc, int s, int mode, double freq,
                                                  double phase_over_pi, const __grid_constant__ RsMaps maps) {
@@ -325,7 +336,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   //    the stencil rows of the stage input (awaited only after the x
   //    transform).  Tensor copies are issued by thread 0: the spectrum box
   //    (layout A) and twelve boxes of stencil rows.
-  if constexpr (TS || TT) {
+  if constexpr (SL || TT) {
     if (threadIdx.x == 0) {
       mbar_init(&bars[0]);
       mbar_init(&bars[1]);
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      if constexpr (TS) {
+      if constexpr (SL) {
         mbar_expect_tx(&bars[0], 3 * (L + 1) * ROWS * 8);
         tma_load_4d(sm, &maps.spec, y0, z, 0, 0, &bars[0]);
       }
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       }
     }
   }
-  if constexpr (!TS) {
+  if constexpr (!SL) {
     for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
       const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
       const int y = y0 + r;
@@ -421,10 +432,10 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   //    rows of pitch L + 1 (layout B) on both paths
   using A = LayA<L, ROWS>;
   using Bl = LayB<L>;
-  using LIn = typename std::conditional<TS, A, Bl>::type;
+  using LIn = typename std::conditional<SL, A, Bl>::type;
   if constexpr (TT) asm volatile("cp.async.wait_all;\n" ::: "memory");
   else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-  if constexpr (TS) {
+  if constexpr (SL) {
     if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[0]);
     __syncthreads();
     if (!tma_ok) {   // uniform; the copies in flight land before the block ends
@@ -441,7 +452,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   }
   for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
     // (consecutive threads on consecutive pencils in layout A)
-    const int pen = TS ? e % (3 * ROWS) : e / (L / 2 + 1), k = TS ? e / (3 * ROWS) : e % (L / 2 + 1);
+    const int pen = SL ? e % (3 * ROWS) : e / (L / 2 + 1), k = SL ? e / (3 * ROWS) : e % (L / 2 + 1);
     const int ia = LIn::at(pen, k), ib = LIn::at(pen, L - k);
     const float2 xa = sm[ia], xb = sm[ib];
     float2 za, zb;
@@ -595,7 +606,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       sw[2 * (2 * ROWS + r) * PST + x] = msat * n2;
     }
     __syncthreads();
-    if constexpr (TS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
+    if constexpr (SS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
     else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
     return;
   }
@@ -659,40 +670,58 @@ struct RsCfg {
   static constexpr int NT = NT0 < 64 ? 64 : (NT0 > 512 ? 512 : NT0);
 };
 
+template <int L, int ROWS, bool SL, bool SS, bool TT>
+void launch_row(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int s, int mode, double freq,
+                double ph, cudaStream_t st) {
+  using C = RsCfg<L, ROWS>;
+  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz);
+  StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
+  k_rs_row<L, ROWS, C::NT, SL, SS, TT><<<grid, C::NT, RsSmem<L, ROWS>::BYTES, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s,
+                                                                                    mode, freq, ph, maps);
+}
+
 template <int L, int ROWS>
 void launch_rs(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
                double freq, double phase, cudaStream_t st) {
   using C = RsCfg<L, ROWS>;
-  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz);
-  StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
+  constexpr bool SPEC = rs_spec_shape<L, ROWS>(), STEN = rs_sten_shape<L>();
+  const bool spec = SPEC && maps.ok_spec, sten = STEN && maps.ok_sten;
   const double ph = phase / 3.14159265358979323846;
-  constexpr int SB = RsSmem<L, ROWS>::BYTES;
-  if constexpr (rs_tma_shape<L, ROWS>()) {
-    if (maps.ok) {
-      if (kind == 0)
-        k_rs_prep<L, ROWS, C::NT, kRsTS><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s, maps);
-      else
-        k_rs_row<L, ROWS, C::NT, kRsTS, kRsTT><<<grid, C::NT, SB, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq,
-                                                                        ph, maps);
-      return;
+  if (kind == 0) {
+    dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz);
+    StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
+    if constexpr (SPEC && kRsPS) {
+      if (spec) {
+        k_rs_prep<L, ROWS, C::NT, true><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s, maps);
+        return;
+      }
     }
-  }
-  if (kind == 0)
     k_rs_prep<L, ROWS, C::NT, false><<<grid, C::NT, 0, st>>>(g, b, rs_ptrs(b), b.st, sc, s, maps);
-  else
-    k_rs_row<L, ROWS, C::NT, false, false><<<grid, C::NT, SB, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq, ph,
-                                                                    maps);
+    return;
+  }
+  if constexpr (SPEC && STEN) {
+    if (spec && sten) return launch_row<L, ROWS, kRsSL, kRsSS, kRsTT>(g, b, T, maps, s, mode, freq, ph, st);
+  }
+  if constexpr (STEN) {
+    if (sten) return launch_row<L, ROWS, false, false, kRsTT>(g, b, T, maps, s, mode, freq, ph, st);
+  }
+  launch_row<L, ROWS, false, false, false>(g, b, T, maps, s, mode, freq, ph, st);
+}
+
+template <int L, int ROWS, bool SL, bool SS, bool TT>
+cudaError_t prepare_row() {
+  return cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT, SL, SS, TT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, RsSmem<L, ROWS>::BYTES);
 }
 
 template <int L, int ROWS>
 cudaError_t prepare_rs() {
-  constexpr int SB = RsSmem<L, ROWS>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT, false, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SB);
-  if constexpr (rs_tma_shape<L, ROWS>()) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_rs_row<L, ROWS, RsCfg<L, ROWS>::NT, kRsTS, kRsTT>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, SB);
+  cudaError_t e = prepare_row<L, ROWS, false, false, false>();
+  if constexpr (rs_sten_shape<L>()) {
+    if (e == cudaSuccess) e = prepare_row<L, ROWS, false, false, kRsTT>();
+  }
+  if constexpr (rs_spec_shape<L, ROWS>() && rs_sten_shape<L>()) {
+    if (e == cudaSuccess) e = prepare_row<L, ROWS, kRsSL, kRsSS, kRsTT>();
   }
   return e;
 }
@@ -775,40 +804,43 @@ cudaError_t prepare_rowstage(const Geom& g) {
   }
 }
 
-// TMA path conditions: a row-kernel shape with rs_tma_shape (32 <= L <= 128,
-// >= 8 rows per block), row strides of nx floats and ny complex values that
-// are multiples of 16 bytes, and no periodic y (the halo rows would wrap).
+// Tensor-copy conditions.  Spectrum box: a shape with rs_spec_shape (32 <=
+// L <= 128, >= 8 rows per block) and rows of ny complex values whose stride
+// is a multiple of 16 bytes (ny even).  Stencil rows: 32 <= L <= 256, rows of
+// nx floats with a 16-byte multiple stride (nx % 4 == 0), y not periodic (the
+// halo rows would wrap).
 void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m) {
   std::memset(m, 0, sizeof(RsMaps));
   const int L = g.lx, rows = rs_rows(g);
-  if (!g.fused || L < 32 || L > 128 || rows < 8 || g.nx % 4 != 0 || g.ny % 2 != 0 || g.pbcy || g.pbcx) return;
-  if (!b.spec || !b.ms || !b.ms2 || !b.code) return;
-  bool ok = true;
-  {
+  if (!g.fused || g.pbcx || !b.spec || !b.ms || !b.ms2 || !b.code) return;
+  if (L >= 32 && L <= 128 && rows >= 8 && g.ny % 2 == 0) {
     const cuuint64_t dims[4] = {(cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)g.hx, 3};
     const cuuint64_t st[3] = {(cuuint64_t)g.ny * 8, (cuuint64_t)g.nz * g.ny * 8, (cuuint64_t)g.hx * g.nz * g.ny * 8};
     const cuuint32_t box[4] = {(cuuint32_t)rows, 1, (cuuint32_t)(L + 1), 3};
-    ok = ok && encode(&m->spec, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, b.spec, dims, st, box);
+    m->ok_spec = encode(&m->spec, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, b.spec, dims, st, box) ? 1 : 0;
   }
-  {
-    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
-    const cuuint64_t st[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.ny * g.nx * 4, (cuuint64_t)g.n * 4};
-    const cuuint32_t own[4] = {(cuuint32_t)L, (cuuint32_t)(rows + 2), 1, 1};
-    const cuuint32_t pl[4] = {(cuuint32_t)L, (cuuint32_t)rows, 1, 1};
-    ok = ok && encode(&m->ms_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms, dims, st, own);
-    ok = ok && encode(&m->ms_pl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms, dims, st, pl);
-    ok = ok && encode(&m->ms2_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms2, dims, st, own);
-    ok = ok && encode(&m->ms2_pl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms2, dims, st, pl);
+  if (L >= 32 && L <= 256 && g.nx % 4 == 0 && !g.pbcy) {
+    bool ok = true;
+    {
+      const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+      const cuuint64_t st[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.ny * g.nx * 4, (cuuint64_t)g.n * 4};
+      const cuuint32_t own[4] = {(cuuint32_t)L, (cuuint32_t)(rows + 2), 1, 1};
+      const cuuint32_t pl[4] = {(cuuint32_t)L, (cuuint32_t)rows, 1, 1};
+      ok = ok && encode(&m->ms_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms, dims, st, own);
+      ok = ok && encode(&m->ms_pl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms, dims, st, pl);
+      ok = ok && encode(&m->ms2_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms2, dims, st, own);
+      ok = ok && encode(&m->ms2_pl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.ms2, dims, st, pl);
+    }
+    {
+      const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+      const cuuint64_t st[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.ny * g.nx * 4};
+      const cuuint32_t own[3] = {(cuuint32_t)L, (cuuint32_t)(rows + 2), 1};
+      const cuuint32_t pl[3] = {(cuuint32_t)L, (cuuint32_t)rows, 1};
+      ok = ok && encode(&m->code_own, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, b.code, dims, st, own);
+      ok = ok && encode(&m->code_pl, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, b.code, dims, st, pl);
+    }
+    m->ok_sten = ok ? 1 : 0;
   }
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-    const cuuint64_t st[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.ny * g.nx * 4};
-    const cuuint32_t own[3] = {(cuuint32_t)L, (cuuint32_t)(rows + 2), 1};
-    const cuuint32_t pl[3] = {(cuuint32_t)L, (cuuint32_t)rows, 1};
-    ok = ok && encode(&m->code_own, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, b.code, dims, st, own);
-    ok = ok && encode(&m->code_pl, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, b.code, dims, st, pl);
-  }
-  m->ok = ok ? 1 : 0;
 }
 
 // kind 0: prep of stage s; kind 1: row kernel of stage s with mode 0 (first
