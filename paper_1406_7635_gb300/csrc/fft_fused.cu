@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
   const int ry = rank % g.cly, rz = rank / g.cly;
   const int kx = (blockIdx.x / CL) % g.hx;
+  // the spectrum comes from the previous kernel (programmatic dependent
+  // launch: wait for it, then let the next kernel's blocks be scheduled)
+  grid_dependency_wait();
   // 1. load the plane (asynchronous copies, all in flight at once); rows and
   //    columns past the grid are zero
   // (32-bit offsets: one instance's spectrum, 3 hx nz ny < 2^31 points)
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   const int h0 = rz * H;                     // first row of my half
   const int cstride = g.hx * g.nz * g.ny;
   float2* const plane = spec + kx * g.nz * g.ny;
+  grid_dependency_wait();   // the spectrum comes from the previous kernel
   // 1. load my half of the rows
   for (int e = threadIdx.x; e < 3 * PH; e += NT) {
     const int y = e % LY, i = (e / LY) % H, c = e / PH, z = h0 + i;
@@ -675,13 +679,15 @@ void launch_yz_cluster(K kern, bool& attr_set, size_t smem, int nt, const Geom& 
   cfg.blockDim = dim3(nt);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = pdl_yz(g) ? 1 : 0;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kern, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st, ba);
 }
 

@@ -344,10 +344,6 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      if constexpr (SL) {
-        mbar_expect_tx(&bars[0], 3 * (L + 1) * ROWS * 8);
-        tma_load_4d(sm, &maps.spec, y0, z, 0, 0, &bars[0]);
-      }
       if constexpr (TT) {
         mbar_expect_tx(&bars[1], 16 * NR * L);
         const CUtensorMap* own = (s & 1) ? &maps.ms2_own : &maps.ms_own;
@@ -364,15 +360,6 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
         tma_load_3d(scode + (ROWS + 2) * L, &maps.code_pl, 0, y0, zm, &bars[1]);
         tma_load_3d(scode + (2 * ROWS + 2) * L, &maps.code_pl, 0, y0, zp, &bars[1]);
       }
-    }
-  }
-  if constexpr (!SL) {
-    for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
-      const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
-      const int y = y0 + r;
-      float2* dst = sm + (c * ROWS + r) * PST + k;
-      if (y < g.ny) cp_async8(dst, b.spec + tix(g, c, k, z, y));
-      else *dst = make_float2(0.f, 0.f);
     }
   }
   load_tables<L, NT>(twl, tw2, b.tw);
@@ -428,12 +415,32 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     av[q][1] = a1;
     av[q][2] = a2;
   }
+  // the spectrum is the previous kernel's output (programmatic dependent
+  // launch: everything above overlaps its last blocks)
+  grid_dependency_wait();
+  if constexpr (SL) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&bars[0], 3 * (L + 1) * ROWS * 8);
+      tma_load_4d(sm, &maps.spec, y0, z, 0, 0, &bars[0]);
+    }
+  } else {
+    for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
+      const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
+      const int y = y0 + r;
+      float2* dst = sm + (c * ROWS + r) * PST + k;
+      if (y < g.ny) cp_async8(dst, b.spec + tix(g, c, k, z, y));
+      else *dst = make_float2(0.f, 0.f);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   // 2. x C2R of the demag spectrum rows (3 components); the output is in
   //    rows of pitch L + 1 (layout B) on both paths
   using A = LayA<L, ROWS>;
   using Bl = LayB<L>;
   using LIn = typename std::conditional<SL, A, Bl>::type;
-  if constexpr (TT) asm volatile("cp.async.wait_all;\n" ::: "memory");
+  // (groups: tables, then the stencil rows unless TT, then the spectrum
+  // unless SL; only the stencil group may stay in flight)
+  if constexpr (TT || !SL) asm volatile("cp.async.wait_all;\n" ::: "memory");
   else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
   if constexpr (SL) {
     if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[0]);
@@ -674,10 +681,19 @@ template <int L, int ROWS, bool SL, bool SS, bool TT>
 void launch_row(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int s, int mode, double freq,
                 double ph, cudaStream_t st) {
   using C = RsCfg<L, ROWS>;
-  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz);
   StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
-  k_rs_row<L, ROWS, C::NT, SL, SS, TT><<<grid, C::NT, RsSmem<L, ROWS>::BYTES, st>>>(g, b, T, rs_ptrs(b), b.st, sc, s,
-                                                                                    mode, freq, ph, maps);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((g.ny + ROWS - 1) / ROWS, g.nz);
+  cfg.blockDim = dim3(C::NT);
+  cfg.dynamicSmemBytes = RsSmem<L, ROWS>::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_row(g) ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_rs_row<L, ROWS, C::NT, SL, SS, TT>, g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq, ph,
+                     maps);
 }
 
 template <int L, int ROWS>
