@@ -78,6 +78,7 @@ struct mm_ctx {
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   DevState* st_host = nullptr;   // pinned mirror
+  bool st_fresh = false;         // st_host equals the device state (no stepping kernel since)
   int fixed_cap = 0;
   int fixed_n = 0;   // host copy of the replay length
   long long launches = 0;        // kernels launched (host count)
@@ -98,14 +99,20 @@ namespace {
 int read_state(mm_ctx* c) {
   MM_CUDA(cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
   MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->st_fresh = true;
   return MM_OK;
 }
 
 int write_state(mm_ctx* c) {
   MM_CUDA(cudaMemcpyAsync(c->b.st, c->st_host, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
   MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->st_fresh = true;
   return MM_OK;
 }
+
+// the host mirror of the device state, read back only if a stepping kernel
+// may have changed it since the last transfer
+int current_state(mm_ctx* c) { return c->st_fresh ? MM_OK : read_state(c); }
 
 // Derived float tables from the float64 host parameters.
 int flush_luts(mm_ctx* c) {
@@ -288,6 +295,7 @@ int drive(mm_ctx* c, int mode, long long nsteps, double t_end) {
   if (rc) return rc;
   rc = build_graph(c);
   if (rc) return rc;
+  c->st_fresh = false;   // the stepping kernels write the device state
   launch_begin_mode(c->b, mode, nsteps, t_end, c->stream);
   c->launches += 1;
   if (!c->k1_valid) enqueue_k1(c);   // no-op on the device if begin found nothing to do
@@ -588,7 +596,7 @@ int mm_enable_terms(mm_ctx* c, int demag, int exch, int anis, int zeeman, int pr
 static int set_m_common(mm_ctx* c, const float* src, cudaMemcpyKind kind) {
   int rc = flush_luts(c);
   if (rc) return rc;
-  rc = read_state(c);
+  rc = current_state(c);
   if (rc) return rc;
   float* dst = c->b.m[c->st_host->parity];
   MM_CUDA(cudaMemcpyAsync(dst, src, 3 * (size_t)c->g.n * sizeof(float), kind, c->stream));
@@ -611,7 +619,7 @@ int mm_set_m_device(mm_ctx* c, const float* m) {
 }
 
 static int get_m_common(mm_ctx* c, float* dst, cudaMemcpyKind kind) {
-  int rc = read_state(c);
+  int rc = current_state(c);
   if (rc) return rc;
   MM_CUDA(cudaMemcpyAsync(dst, c->b.m[c->st_host->parity], 3 * (size_t)c->g.n * sizeof(float), kind, c->stream));
   MM_CUDA(cudaStreamSynchronize(c->stream));

@@ -228,8 +228,13 @@ class Context:
         a = np.ascontiguousarray(m, dtype=np.float32).reshape((3,) + self.shape)
         _check(mm_set_m(self.h, _ptr(a)))
 
-    def get_m(self):
-        out = np.zeros((3,) + self.shape, dtype=np.float32)
+    def get_m(self, out=None):
+        """m as float32 [3][nz][ny][nx]; into `out` (a C-contiguous float32
+        array of that shape, e.g. in pinned memory) when given."""
+        if out is None:
+            out = np.zeros((3,) + self.shape, dtype=np.float32)
+        elif out.dtype != np.float32 or out.shape != (3,) + self.shape or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float32 array of shape (3, nz, ny, nx)")
         _check(mm_get_m(self.h, _ptr(out)))
         return out
 
