@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ 
   const int y0 = blockIdx.x * ROWS, z = blockIdx.y, c = blockIdx.z % 3;
   twiddles_async<NT>(twl, tw, L, kTwN / L);
   twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
+  grid_dependency_wait();   // the spectrum comes from the y/z kernel
   for (int e = threadIdx.x; e < ROWS * (L + 1); e += NT) {
     const int r = e % ROWS, k = e / ROWS, y = y0 + r;
     if (y < g.ny) cp_async_f2(&s[r * PST + k], spec + tidx(g, c, k, z, y));
@@ -627,8 +628,17 @@ void run_fx_rows(const Geom& g, const Buffers& b, const float* m, cudaStream_t s
 template <int L, int ROWS>
 void run_ix_rows(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
   constexpr int NT = RowNT<L, ROWS>::NT;
-  dim3 grid((g.ny + ROWS - 1) / ROWS, g.nz, 3 * ba.count);
-  k_ix_t<L, ROWS, NT><<<grid, NT, 0, s>>>(g, b.spec, b.bd, b.tw, b.st, ba);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((g.ny + ROWS - 1) / ROWS, g.nz, 3 * ba.count);
+  cfg.blockDim = dim3(NT);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_ix_t<L, ROWS, NT>, g, (const float2*)b.spec, b.bd, (const float2*)b.tw,
+                     (const DevState*)b.st, ba);
 }
 template <int L>
 void run_fx_t(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
@@ -668,7 +678,7 @@ struct YzCfg {
 // launch every configuration first)
 template <typename K>
 void launch_yz_cluster(K kern, bool& attr_set, size_t smem, int nt, const Geom& g, const Buffers& b, cudaStream_t s,
-                       const BatchArgs& ba) {
+                       const BatchArgs& ba, bool pdl) {
   if (!attr_set) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
@@ -685,25 +695,25 @@ void launch_yz_cluster(K kern, bool& attr_set, size_t smem, int nt, const Geom& 
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = pdl_yz(g) ? 1 : 0;
+  attr[1].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kern, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st, ba);
 }
 
 template <int LY, int LZ>
-void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
+void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba, bool pdl) {
   using C = YzCfg<LY, LZ>;
   if constexpr (LZ >= 4) {
     // z-split clusters share the y transforms between the two z classes
     if (g.clz == 2) {
       static bool set2 = false;
-      launch_yz_cluster(k_yz2<LY, LZ, C::NT>, set2, C::SMEM, C::NT, g, b, s, ba);
+      launch_yz_cluster(k_yz2<LY, LZ, C::NT>, set2, C::SMEM, C::NT, g, b, s, ba, pdl);
       return;
     }
   }
   static bool set1 = false;
-  launch_yz_cluster(k_yz<LY, LZ, C::NT>, set1, C::SMEM, C::NT, g, b, s, ba);
+  launch_yz_cluster(k_yz<LY, LZ, C::NT>, set1, C::SMEM, C::NT, g, b, s, ba, pdl);
 }
 
 __global__ void k_kt_transpose(Geom g, const float* __restrict__ kt, float* __restrict__ ktf) {
@@ -791,27 +801,28 @@ void launch_demag_fused(const Geom& g, const Buffers& b, const float* m, cudaStr
   launch_demag_fused_batch(g, b, m, s, BatchArgs{1, nullptr, nullptr, 0});
 }
 
-static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba);
+static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba, bool pdl);
 
 void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s) {
-  launch_yz_batch(g, b, s, BatchArgs{1, nullptr, nullptr, 0});
+  launch_yz_batch(g, b, s, BatchArgs{1, nullptr, nullptr, 0}, pdl_yz(g));
 }
 
 void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, cudaStream_t s, const BatchArgs& ba) {
 #define CALL_FX(LL) run_fx_t<LL>(g, b, m, s, ba)
   MM_ROWL(g.lx, CALL_FX)
 #undef CALL_FX
-  launch_yz_batch(g, b, s, ba);
+  // (the y/z and x C2R kernels start while their predecessor drains)
+  launch_yz_batch(g, b, s, ba, true);
 #define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
   MM_ROWL(g.lx, CALL_IX)
 #undef CALL_IX
 }
 
-static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba) {
+static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba, bool pdl) {
   const int key = g.ly * 100 + g.lz;
   switch (key) {
 #define YZ(LY, LZ) \
-  case LY * 100 + LZ: run_yz<LY, LZ>(g, b, s, ba); break;
+  case LY * 100 + LZ: run_yz<LY, LZ>(g, b, s, ba, pdl); break;
     YZ(16, 1) YZ(32, 1) YZ(64, 1) YZ(128, 1) YZ(256, 1) YZ(512, 1) YZ(1024, 1)
     YZ(16, 2) YZ(32, 2) YZ(64, 2) YZ(128, 2) YZ(256, 2) YZ(512, 2) YZ(1024, 2)
     YZ(16, 4) YZ(32, 4) YZ(64, 4) YZ(128, 4) YZ(256, 4) YZ(512, 4) YZ(1024, 4)
