@@ -441,14 +441,19 @@ def run_surrogate(args, local_rank, steps=40):
             "guarded_final_m_max_err_vs_exact": float(np.abs(m_guard - m_exact).max())}
 
 
-def oracle_cpu_run(name, budget_s, max_steps):
-    """The float64 oracle on the same workload: kernel set-up untimed, then
-    accepted adaptive RK45 steps until the time budget is spent."""
+def oracle_cpu_run(name, budget_s, max_steps, warmup=0, warmup_budget_s=30.0):
+    """The float64 oracle on the same workload: kernel set-up untimed, up to
+    `warmup` untimed adaptive RK45 steps (within warmup_budget_s), then
+    accepted steps until the time budget is spent.  Returns (problem, timed
+    steps, seconds, warm-up steps done)."""
     from oracle.rk45 import RK45
     p = WORKLOADS[name]()
     s = RK45(p)
-    s.field.torque(s.m, 0.0)          # first stage (untimed, like the GPU's warm-up)
-    s.k1 = s.field.torque(s.m, 0.0)
+    s.k1 = s.field.torque(s.m, 0.0)   # first stage (untimed, like the GPU's warm-up)
+    w0, done_w = time.perf_counter(), 0
+    while done_w < warmup and time.perf_counter() - w0 < warmup_budget_s:
+        s.adaptive_step()
+        done_w += 1
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps:
@@ -457,18 +462,18 @@ def oracle_cpu_run(name, budget_s, max_steps):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return p, steps, dt
+    return p, steps, dt, done_w
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
     budget = float(os.environ.get("MM_REF_BUDGET_S", 60))
-    p, steps, dt = oracle_cpu_run(args.workload, budget, max(args.steps, 1))
+    p, steps, dt, warm = oracle_cpu_run(args.workload, budget, max(args.steps, 1), warmup=args.warmup)
     v = p.ncells * steps / dt
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "cell-steps/s", "n_gpus": world,
-        "steps": steps, "warmup": 0, "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [p.nx, p.ny, p.nz], "cells": p.ncells},
         "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
@@ -506,7 +511,7 @@ def main():
     out = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         budget = float(os.environ.get("MM_CPU_BUDGET_S", 20))
-        p, steps, dt = oracle_cpu_run(args.workload, budget, 1000)
+        p, steps, dt, _ = oracle_cpu_run(args.workload, budget, 1000)
         out["cpu_baseline"] = {"value": p.ncells * steps / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                                "sample": f"{steps} accepted RK45 steps of the full {args.workload} grid "
                                          f"(float64 numpy oracle, kernel set-up untimed)"}

@@ -21,6 +21,7 @@ def _free_port():
 class _Args:
     workload = "film_64x16x1"
     steps = 1
+    warmup = 3
 
 
 def _worker(rank, world, port, q):
