@@ -145,10 +145,12 @@ __host__ __device__ constexpr int ns_of(int L, int p) {
 // __syncwarp() orders reads before writes) instead of the whole block.
 // IS: stride between the pencils of one group (default 1), so that
 // base = (q / INNER) * BS + (q % INNER) * IS.
+// nin (first pass only): input elements i >= nin are zero and not read
+// (a pruned transform of a zero-padded row).
 template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, bool WARP = false,
           int IS = 1>
 __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw,
-                                              const float2* __restrict__ pre = nullptr) {
+                                              const float2* __restrict__ pre = nullptr, int nin = L) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
   constexpr int PER = (TOT + NT - 1) / NT;
@@ -161,7 +163,8 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
       const int p = b % NP, j = b / NP;
       const int base = (p / INNER) * BS + (p % INNER) * IS;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[base + (j + r * NB) * ES];
+      for (int r = 0; r < R; ++r)
+        v[q][r] = (NS > 1 || j + r * NB < nin) ? s[base + (j + r * NB) * ES] : make_float2(0.f, 0.f);
       if (NS == 1 && pre != nullptr) {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[q][r] = cmul(v[q][r], pre[j + r * NB]);
@@ -202,18 +205,20 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL = kTwN, int IS = 1, int P = 0,
           bool DONE = (P >= npasses(L))>
 struct FftG;
+// (nin: the first pass reads only input elements i < nin, the rest are zero)
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int IS, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, false> {
   __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw,
-                                             const float2* __restrict__ pre = nullptr) {
-    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL, false, IS>(s, tw,
-                                                                                            P == 0 ? pre : nullptr);
+                                             const float2* __restrict__ pre = nullptr, int nin = L) {
+    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL, false, IS>(
+        s, tw, P == 0 ? pre : nullptr, P == 0 ? nin : L);
     FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P + 1>::run(s, tw);
   }
 };
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int IS, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, true> {
-  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr) {}
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr,
+                                             int = L) {}
 };
 
 // The same transform on pencils owned by the calling warp (all 32 lanes call
@@ -251,7 +256,7 @@ struct Lay {
 // writing its outputs in layout LO over the same buffer (every read of the
 // pass completes before the barrier, every write comes after it).
 template <int L, int R, int NS, int DIR, int NP, int NT, class LI, class LO, int TWL>
-__device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restrict__ tw, int nin = L) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
   constexpr int PER = (TOT + NT - 1) / NT;
@@ -262,7 +267,8 @@ __device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restr
     if (TOT % NT == 0 || b < TOT) {
       const int p = b % NP, j = b / NP;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[LI::at(p, j + r * NB)];
+      for (int r = 0; r < R; ++r)
+        v[q][r] = (NS > 1 || j + r * NB < nin) ? s[LI::at(p, j + r * NB)] : make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
@@ -291,22 +297,23 @@ __device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restr
 
 // Full length-L transform of NP pencils whose first pass reads layout LI,
 // whose last pass writes layout LO and whose other passes use layout LM.
+// nin: the first pass reads only input elements i < nin (the rest are zero).
 // Callers synchronise before; ends with __syncthreads().
 template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P = 0,
           bool DONE = (P >= npasses(L))>
 struct FftX;
 template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P>
 struct FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P, false> {
-  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw) {
+  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw, int nin = L) {
     using In = typename std::conditional<P == 0, LI, LM>::type;
     using Out = typename std::conditional<P + 1 == npasses(L), LO, LM>::type;
-    stockham_pass_x<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, In, Out, TWL>(s, tw);
+    stockham_pass_x<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, In, Out, TWL>(s, tw, P == 0 ? nin : L);
     FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P + 1>::run(s, tw);
   }
 };
 template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P>
 struct FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P, true> {
-  __device__ __forceinline__ static void run(float2*, const float2* __restrict__) {}
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, int = L) {}
 };
 
 // copy W_L^i (i < L) out of the global 2048-entry table into shared memory

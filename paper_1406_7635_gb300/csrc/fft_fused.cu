@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
   twiddles_async<NT>(twl, tw, L, kTwN / L);
   twiddles_async<NT>(tw2, tw, L + 1, kTwN / (2 * L));
   const bool even = (g.nx & 1) == 0;
+  const int nin = (g.nx + 1) / 2;   // complex inputs n >= nin are zero padding (not stored, not read)
   const float* __restrict__ mc = m + c * (int)g.n;   // this component (3 n < 2^31)
   for (int e = threadIdx.x; e < ROWS * L; e += NT) {
     const int r = e / L, n = e % L, y = y0 + r;
@@ -84,11 +85,11 @@ __global__ void __launch_bounds__(NT) k_fx_t(Geom g, const float* __restrict__ m
         if (x1 < g.nx) v.y = cell_msat_f(lut, mask, region, cell0 + x1) * mc[cell0 + x1];
       }
     }
-    s[r * PST + n] = v;
+    if (n < nin) s[r * PST + n] = v;
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  FftG<L, -1, ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  FftG<L, -1, ROWS, NT, 1, PST, 1, L>::run(s, twl, nullptr, nin);
   // X_k = E_k + W_P^k O_k; store with consecutive threads on consecutive y
   for (int e = threadIdx.x; e < ROWS * (L + 1); e += NT) {
     const int r = e % ROWS, k = e / ROWS, y = y0 + r;

@@ -31,12 +31,13 @@ __device__ __forceinline__ int tix(const Geom& g, int c, int kx, int z, int y) {
   return ((c * g.hx + kx) * g.nz + z) * g.ny + y;
 }
 
-// x R2C of the packed rows in s (3 * ROWS pencils) into the spectrum
+// x R2C of the packed rows in s (3 * ROWS pencils) into the spectrum; the
+// complex inputs n >= (nx + 1) / 2 are the zero padding and are not read
 template <int L, int ROWS, int NT>
 __device__ __forceinline__ void rows_fx(const Geom& g, float2* s, const float2* twl, const float2* tw2, float2* spec,
                                         int y0, int z) {
   constexpr int PST = L + 1;
-  FftG<L, -1, 3 * ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  FftG<L, -1, 3 * ROWS, NT, 1, PST, 1, L>::run(s, twl, nullptr, (g.nx + 1) / 2);
   for (int e = threadIdx.x; e < 3 * ROWS * (L + 1); e += NT) {
     const int r = e % ROWS, k = (e / ROWS) % (L + 1), c = e / (ROWS * (L + 1));
     const int y = y0 + r;
@@ -122,10 +123,10 @@ using LayB = Lay<1, L + 1, 1>;
 // X_k = E_k + W_2L^k O_k runs on the pairs (k, L - k) in place (X_L beside),
 // rows past the grid are clipped by the store.
 template <int L, int ROWS, int NT>
-__device__ __forceinline__ void rows_fx_tma(float2* s, const float2* twl, const float2* tw2, const CUtensorMap* map,
-                                            int y0, int z) {
+__device__ __forceinline__ void rows_fx_tma(const Geom& g, float2* s, const float2* twl, const float2* tw2,
+                                            const CUtensorMap* map, int y0, int z) {
   using A = LayA<L, ROWS>;
-  FftX<L, -1, 3 * ROWS, NT, LayB<L>, A, A, L>::run(s, twl);
+  FftX<L, -1, 3 * ROWS, NT, LayB<L>, A, A, L>::run(s, twl, (g.nx + 1) / 2);
   for (int e = threadIdx.x; e < 3 * ROWS * (L / 2 + 1); e += NT) {
     const int pen = e % (3 * ROWS), k = e / (3 * ROWS);
     const int ia = A::at(pen, k), ib = A::at(pen, (L - k) & (L - 1));
@@ -176,8 +177,10 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   const int par = st->parity;
   const float* __restrict__ m = par ? p.m1 : p.m0;
   float* __restrict__ out = stage_buf(b, s);
-  for (int e = threadIdx.x; e < ROWS * 2 * L; e += NT) {
-    const int x = e % (2 * L), r = e / (2 * L), y = y0 + r;
+  // (x >= nx rounded up to even is zero padding, never read by the transform)
+  const int xw = (g.nx + 1) & ~1;
+  for (int e = threadIdx.x; e < ROWS * xw; e += NT) {
+    const int x = e % xw, r = e / xw, y = y0 + r;
     float v[3] = {0.f, 0.f, 0.f};
     if (y < g.ny && x < g.nx) {
       const int n = (int)g.n, i = (z * g.ny + y) * g.nx + x;
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  if constexpr (SS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
+  if constexpr (SS) rows_fx_tma<L, ROWS, NT>(g, sm, twl, tw2, &maps.spec, y0, z);
   else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
 }
 
@@ -588,11 +591,11 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     __syncthreads();   // every thread is done reading B_demag from sm
     float* sw = reinterpret_cast<float*>(sm);
     float* __restrict__ nxt = stage_buf(b, s + 1);
-    // x padding (x >= nx) and rows past the grid are zero
-    for (int e = threadIdx.x; e < 3 * ROWS * 2 * L; e += NT) {
-      const int x = e % (2 * L), row = e / (2 * L), r = row % ROWS;
-      if (x >= g.nx || y0 + r >= g.ny) sw[2 * row * PST + x] = 0.f;
-    }
+    // the transform reads x < nx rounded up to even: with an odd nx the
+    // element x = nx is padding and must be zero (rows past the grid are
+    // transformed but never stored)
+    if (g.nx & 1)
+      for (int row = threadIdx.x; row < 3 * ROWS; row += NT) sw[2 * row * PST + g.nx] = 0.f;
     const float a = sc->ah[s + 1][s];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
@@ -613,7 +616,7 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       sw[2 * (2 * ROWS + r) * PST + x] = msat * n2;
     }
     __syncthreads();
-    if constexpr (SS) rows_fx_tma<L, ROWS, NT>(sm, twl, tw2, &maps.spec, y0, z);
+    if constexpr (SS) rows_fx_tma<L, ROWS, NT>(g, sm, twl, tw2, &maps.spec, y0, z);
     else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
     return;
   }
