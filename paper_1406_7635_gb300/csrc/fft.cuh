@@ -146,11 +146,12 @@ __host__ __device__ constexpr int ns_of(int L, int p) {
 // IS: stride between the pencils of one group (default 1), so that
 // base = (q / INNER) * BS + (q % INNER) * IS.
 // nin (first pass only): input elements i >= nin are zero and not read
-// (a pruned transform of a zero-padded row).
+// (a pruned transform of a zero-padded row); nout (last pass only): output
+// elements i >= nout are not needed and not written (a cropped transform).
 template <int L, int R, int NS, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, bool WARP = false,
           int IS = 1>
 __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw,
-                                              const float2* __restrict__ pre = nullptr, int nin = L) {
+                                              const float2* __restrict__ pre = nullptr, int nin = L, int nout = L) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
   constexpr int PER = (TOT + NT - 1) / NT;
@@ -192,7 +193,8 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
       Dft<R, DIR>::run(v[q]);
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[base + (o + r * NS) * ES] = v[q][r];
+      for (int r = 0; r < R; ++r)
+        if (NS * R < L || o + r * NS < nout) s[base + (o + r * NS) * ES] = v[q][r];
     }
   }
   if (WARP) __syncwarp();
@@ -205,20 +207,21 @@ __device__ __forceinline__ void stockham_pass(float2* s, const float2* __restric
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL = kTwN, int IS = 1, int P = 0,
           bool DONE = (P >= npasses(L))>
 struct FftG;
-// (nin: the first pass reads only input elements i < nin, the rest are zero)
+// (nin: the first pass reads only input elements i < nin, the rest are zero;
+// nout: the last pass writes only output elements i < nout)
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int IS, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, false> {
   __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw,
-                                             const float2* __restrict__ pre = nullptr, int nin = L) {
+                                             const float2* __restrict__ pre = nullptr, int nin = L, int nout = L) {
     stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, INNER, BS, ES, TWL, false, IS>(
-        s, tw, P == 0 ? pre : nullptr, P == 0 ? nin : L);
-    FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P + 1>::run(s, tw);
+        s, tw, P == 0 ? pre : nullptr, P == 0 ? nin : L, P + 1 == npasses(L) ? nout : L);
+    FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P + 1>::run(s, tw, nullptr, L, nout);
   }
 };
 template <int L, int DIR, int NP, int NT, int INNER, int BS, int ES, int TWL, int IS, int P>
 struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, true> {
   __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr,
-                                             int = L) {}
+                                             int = L, int = L) {}
 };
 
 // The same transform on pencils owned by the calling warp (all 32 lanes call
@@ -256,7 +259,7 @@ struct Lay {
 // writing its outputs in layout LO over the same buffer (every read of the
 // pass completes before the barrier, every write comes after it).
 template <int L, int R, int NS, int DIR, int NP, int NT, class LI, class LO, int TWL>
-__device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restrict__ tw, int nin = L) {
+__device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restrict__ tw, int nin = L, int nout = L) {
   constexpr int NB = L / R;
   constexpr int TOT = NB * NP;
   constexpr int PER = (TOT + NT - 1) / NT;
@@ -289,7 +292,8 @@ __device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restr
       Dft<R, DIR>::run(v[q]);
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[LO::at(p, o + r * NS)] = v[q][r];
+      for (int r = 0; r < R; ++r)
+        if (NS * R < L || o + r * NS < nout) s[LO::at(p, o + r * NS)] = v[q][r];
     }
   }
   __syncthreads();
@@ -297,23 +301,25 @@ __device__ __forceinline__ void stockham_pass_x(float2* s, const float2* __restr
 
 // Full length-L transform of NP pencils whose first pass reads layout LI,
 // whose last pass writes layout LO and whose other passes use layout LM.
-// nin: the first pass reads only input elements i < nin (the rest are zero).
+// nin: the first pass reads only input elements i < nin (the rest are zero);
+// nout: the last pass writes only output elements i < nout.
 // Callers synchronise before; ends with __syncthreads().
 template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P = 0,
           bool DONE = (P >= npasses(L))>
 struct FftX;
 template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P>
 struct FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P, false> {
-  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw, int nin = L) {
+  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw, int nin = L, int nout = L) {
     using In = typename std::conditional<P == 0, LI, LM>::type;
     using Out = typename std::conditional<P + 1 == npasses(L), LO, LM>::type;
-    stockham_pass_x<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, In, Out, TWL>(s, tw, P == 0 ? nin : L);
-    FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P + 1>::run(s, tw);
+    stockham_pass_x<L, radix_of(L, P), ns_of(L, P), DIR, NP, NT, In, Out, TWL>(s, tw, P == 0 ? nin : L,
+                                                                                P + 1 == npasses(L) ? nout : L);
+    FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P + 1>::run(s, tw, L, nout);
   }
 };
 template <int L, int DIR, int NP, int NT, class LI, class LM, class LO, int TWL, int P>
 struct FftX<L, DIR, NP, NT, LI, LM, LO, TWL, P, true> {
-  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, int = L) {}
+  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, int = L, int = L) {}
 };
 
 // copy W_L^i (i < L) out of the global 2048-entry table into shared memory

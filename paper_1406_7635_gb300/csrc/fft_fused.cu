@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(NT) k_ix_t(Geom g, const float2* __restrict__ 
     if (k != 0 && k != L / 2) s[r * PST + L - k] = zb;
   }
   __syncthreads();
-  FftG<L, 1, ROWS, NT, 1, PST, 1, L>::run(s, twl);
+  FftG<L, 1, ROWS, NT, 1, PST, 1, L>::run(s, twl, nullptr, L, (g.nx + 1) / 2);   // outputs 2n >= nx cropped
   float* __restrict__ oc = out + c * (int)g.n;
   for (int e = threadIdx.x; e < ROWS * L; e += NT) {
     const int r = e / L, n = e % L, y = y0 + r;
@@ -372,15 +372,17 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   // the spectrum comes from the previous kernel (programmatic dependent
   // launch: wait for it, then let the next kernel's blocks be scheduled)
   grid_dependency_wait();
-  // 1. load the plane (asynchronous copies, all in flight at once); rows and
-  //    columns past the grid are zero
+  // 1. load the plane (asynchronous copies, all in flight at once); rows
+  //    past the grid are zero; columns y >= ny are never read (the first y
+  //    pass is pruned to y < ny)
   // (32-bit offsets: one instance's spectrum, 3 hx nz ny < 2^31 points)
   const int cstride = g.hx * g.nz * g.ny;              // component stride of spec
   float2* const plane = spec + kx * g.nz * g.ny;       // this kx plane, component 0
   for (int e = threadIdx.x; e < 3 * PL; e += NT) {
     const int y = e % LY, z = (e / LY) % LZ, c = e / PL;
+    if (y >= g.ny) continue;
     float2* dst = s + c * CS + z * RP + y;
-    if (y < g.ny && z < g.nz) {
+    if (z < g.nz) {
       const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr),
                    "l"(plane + c * cstride + z * g.ny + y));
@@ -397,8 +399,8 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
     constexpr int R0 = LZ / zmid_radix(LZ);
     // (the three components' rows are one array of 3 LZ rows at pitch RP:
     // components 0 and 1 are transformed together, then component 2)
-    FftG<LY, -1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy, ry ? rty : nullptr);
-    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy, ry ? rty : nullptr);
+    FftG<LY, -1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy, ry ? rty : nullptr, g.ny);
+    FftG<LY, -1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy, ry ? rty : nullptr, g.ny);
     if constexpr (R0 > 1) {
       stockham_pass<LZ, R0, 1, -1, 2 * LY, NT, LY, CS, RP, LZ>(s, twz, rz ? rtz : nullptr);
       stockham_pass<LZ, R0, 1, -1, LY, NT, LY, CS, RP, LZ>(s + 2 * CS, twz, rz ? rtz : nullptr);
@@ -410,14 +412,15 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
     // 4. rest of the inverse transforms
     z_inv_tail<LY, LZ, NT, RP, CS, 2>(s, twz);
     z_inv_tail<LY, LZ, NT, RP, CS, 1>(s + 2 * CS, twz);
-    FftG<LY, 1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy);
-    FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy);
+    // (outputs y >= ny are cropped: never stored nor read by the class sum)
+    FftG<LY, 1, 2 * LZ, NT, 1, RP, 1, LY>::run(s, twy, nullptr, LY, g.ny);
+    FftG<LY, 1, LZ, NT, 1, RP, 1, LY>::run(s + 2 * CS, twy, nullptr, LY, g.ny);
   } else {
     // 2-D: the three components are three rows at pitch RP, transformed together
-    FftG<LY, -1, 3, NT, 1, RP, 1, LY>::run(s, twy, ry ? rty : nullptr);
+    FftG<LY, -1, 3, NT, 1, RP, 1, LY>::run(s, twy, ry ? rty : nullptr, g.ny);
     kernel_mul<LY, LZ, RP, CS, LY, NT, 2>(s, kt, g, kx, ry, rz, 0, threadIdx.x);
     __syncthreads();
-    FftG<LY, 1, 3, NT, 1, RP, 1, LY>::run(s, twy);
+    FftG<LY, 1, 3, NT, 1, RP, 1, LY>::run(s, twy, nullptr, LY, g.ny);
   }
   // 5. sum the class contributions across the cluster, each multiplied by
   //    the conjugate of its class twiddle; each block stores one contiguous
@@ -509,11 +512,13 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   const int cstride = g.hx * g.nz * g.ny;
   float2* const plane = spec + kx * g.nz * g.ny;
   grid_dependency_wait();   // the spectrum comes from the previous kernel
-  // 1. load my half of the rows
+  // 1. load my half of the rows (columns y >= ny are never read: the first
+  //    y pass is pruned to y < ny)
   for (int e = threadIdx.x; e < 3 * PH; e += NT) {
     const int y = e % LY, i = (e / LY) % H, c = e / PH, z = h0 + i;
+    if (y >= g.ny) continue;
     float2* dst = s + c * CS + z * RP + y;
-    if (y < g.ny && z < g.nz) {
+    if (z < g.nz) {
       const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr),
                    "l"(plane + c * cstride + z * g.ny + y));
@@ -525,7 +530,7 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   __syncthreads();
   // 2. forward y on my half of the rows of all three components (pencil q:
   //    component q / H, row h0 + q % H), y-class twiddle on load
-  FftG<LY, -1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy, ry ? rty : nullptr);
+  FftG<LY, -1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy, ry ? rty : nullptr, g.ny);
   // 3. my half into the partner's rows at the same positions, which the
   //    partner neither loaded nor transformed (remote stores, no round trip)
   cluster_wait();
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   }
   __syncthreads();
   // 6. inverse y on my half of the rows
-  FftG<LY, 1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy);
+  FftG<LY, 1, 3 * H, NT, H, CS, 1, LY, RP>::run(s + h0 * RP, twy, nullptr, LY, g.ny);   // y >= ny cropped
   // 7. sum over the y classes (cly = 2: the block with the other ry and the
   //    same half) and store; with cly = 2 each block stores half of its rows
   if (g.cly > 1) cluster.sync();

@@ -480,7 +480,8 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
     if (k != 0 && k != L / 2) sm[ib] = zb;
   }
   __syncthreads();
-  FftX<L, 1, 3 * ROWS, NT, LIn, LIn, Bl, L>::run(sm, twl);
+  // (outputs 2n >= nx are cropped: the field code reads x < nx)
+  FftX<L, 1, 3 * ROWS, NT, LIn, LIn, Bl, L>::run(sm, twl, L, (g.nx + 1) / 2);
   if constexpr (TT) {
     if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[1]);
     __syncthreads();
