@@ -227,7 +227,7 @@ def test_larmor_precession_gpu(mm):
 
 @pytest.mark.parametrize("which,nsteps", [("film", 200), ("grains", 60), ("ellipsoid", 30), ("random", 60)])
 def test_lockstep_vs_oracle(mm, which, nsteps):
-    """The spec parity bar: GPU adaptive RK45 for n steps, then the oracle
+    """Trajectory parity: GPU adaptive RK45 for n steps, then the oracle
     replays exactly the GPU's accepted step sizes; m must agree to 1e-5."""
     if which == "film":
         p = film_sp4(64, 16)

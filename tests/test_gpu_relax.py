@@ -100,7 +100,7 @@ def test_relax_stoner_wohlfarth_gpu(mm):
 
 @pytest.mark.parametrize("b", [(10e-3, 20e-3, 0.0), (-24.6e-3, 4.3e-3, 0.0)])
 def test_relaxed_state_vs_oracle(mm, b):
-    """The spec bar for relaxed states: the 32 x 8 SP4-like film
+    """Relaxed-state parity: the 32 x 8 SP4-like film
     (alpha 1) relaxed by relax() on the GPU and by the oracle agree to 1e-3
     in every cell."""
     p = film_sp4(32, 8)
