@@ -1,6 +1,10 @@
 // Fused RK45 stage kernels for the fused convolution layout (spec as
-// [c][kx][z][y]): per attempt, one prep kernel and, per stage, k_yz plus one
-// row kernel, instead of five kernels per stage.
+// [c][kx][z][y]): per attempt, one prep kernel and, per stage, the y/z
+// transform kernel (k_yz2 / k_yz) plus one row kernel, instead of five
+// kernels per stage.  Where the shape allows, the row kernel moves its
+// spectrum box and stencil rows with tensor copies (TMA), and on grids with
+// the z-split y/z kernel it is launched as a programmatic dependent of it
+// (its stencil copies and earlier-stage sums run before the wait).
 //
 // A block owns ROWS complete x-rows (one z plane) of all three components.
 //   k_rs_prep  stage input m_s = m + dt sum_j a_sj k_j for its cells, written
@@ -210,9 +214,10 @@ __global__ void __launch_bounds__(NT) k_rs_prep(Geom g, Buffers b, Ptrs p, const
   else rows_fx<L, ROWS, NT>(g, sm, twl, tw2, b.spec, y0, z);
 }
 
-// Shared-memory layout of the row kernel (dynamic): the demag rows of the
-// block (3 ROWS pencils of L + 1 complex, padded to 16 bytes), then the
-// stencil rows of the stage input [3][NR][L] and their cell codes [NR][L].
+// Shared-memory layout of the row kernel (dynamic, base rounded up to 128
+// bytes): the demag rows of the block (3 ROWS pencils of L + 1 complex,
+// padded to 128 bytes), then the stencil rows of the stage input [3][NR][L]
+// and their cell codes [NR][L].
 // Local stencil rows: 0 .. ROWS+1 are y0-1 .. y0+ROWS of plane z, then ROWS
 // rows y0 .. of plane z-1, then ROWS rows of plane z+1.
 template <int L, int ROWS>
