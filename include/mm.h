@@ -145,7 +145,9 @@ int mm_enable_stt(mm_ctx* ctx, int zhang_li, int slonczewski);
 
 /* Reduced magnetisation m, float32 SoA [3][nz][ny][nx].  The library
  * normalises it per magnetic cell and zeroes it in vacuum.  Setting m
- * invalidates the cached first RK stage. */
+ * invalidates the cached first RK stage, unless the new m equals the current
+ * one bit for bit (e.g. written back as read by mm_get_m): then the call
+ * changes nothing. */
 int mm_set_m(mm_ctx* ctx, const float* m);
 int mm_get_m(mm_ctx* ctx, float* m);
 int mm_set_m_device(mm_ctx* ctx, const float* dm);

@@ -221,6 +221,15 @@ __global__ void k_normalize(Geom g, const uint8_t* __restrict__ mask, const uint
   m[2 * n + i] = z * inv;
 }
 
+// *flag = 1 if the 3 n floats of a and b differ in any bit (the flag is
+// zeroed by the caller; every writer stores the same value)
+__global__ void k_m_differs(long long n3, const float* __restrict__ a, const float* __restrict__ b,
+                            int* __restrict__ flag) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  if (__float_as_uint(a[i]) != __float_as_uint(b[i])) *flag = 1;
+}
+
 __global__ void k_codes(Geom g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ region,
                         const RegionLUT* __restrict__ lut, int* __restrict__ code) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^28
@@ -272,6 +281,10 @@ void launch_error_control(const Geom& g, const Buffers& b, cudaStream_t s) {
 void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const Stt& S, const float* m, int mode,
                         double freq, double phase, cudaStream_t s) {
   k_field_out<<<blocks(g.n), kT, 0, s>>>(g, b, T, S, m, b.st, mode, freq, phase / 3.14159265358979323846);
+}
+
+void launch_m_differs(const Geom& g, const float* a, const float* b, int* flag, cudaStream_t s) {
+  k_m_differs<<<blocks(3 * g.n), kT, 0, s>>>(3 * g.n, a, b, flag);
 }
 
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s) {

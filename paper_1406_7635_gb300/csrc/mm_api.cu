@@ -593,13 +593,31 @@ int mm_enable_terms(mm_ctx* c, int demag, int exch, int anis, int zeeman, int pr
   return MM_OK;
 }
 
+// Setting m to the value it already has (bit for bit, e.g. a host loop that
+// writes back what it read) changes nothing: the cached first RK stage stays
+// valid.  The data go to a scratch buffer first and are compared on the
+// device; otherwise they replace m, are normalised and the cache is dropped.
 static int set_m_common(mm_ctx* c, const float* src, cudaMemcpyKind kind) {
   int rc = flush_luts(c);
   if (rc) return rc;
   rc = current_state(c);
   if (rc) return rc;
   float* dst = c->b.m[c->st_host->parity];
-  MM_CUDA(cudaMemcpyAsync(dst, src, 3 * (size_t)c->g.n * sizeof(float), kind, c->stream));
+  const size_t bytes = 3 * (size_t)c->g.n * sizeof(float);
+  if (c->m_set && c->k1_valid) {
+    int* flag = reinterpret_cast<int*>(c->b.acc + 15);   // (acc[15]: not used by the getters)
+    MM_CUDA(cudaMemcpyAsync(c->b.out, src, bytes, kind, c->stream));
+    MM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    launch_m_differs(c->g, c->b.out, dst, flag, c->stream);
+    MM_CUDA(cudaGetLastError());
+    int differs = 1;
+    MM_CUDA(cudaMemcpyAsync(&differs, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MM_CUDA(cudaStreamSynchronize(c->stream));
+    if (!differs) return MM_OK;
+    MM_CUDA(cudaMemcpyAsync(dst, c->b.out, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    MM_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+  }
   launch_normalize(c->g, c->b, dst, c->stream);
   MM_CUDA(cudaGetLastError());
   MM_CUDA(cudaStreamSynchronize(c->stream));

@@ -231,6 +231,8 @@ void launch_copy_mcur(const Geom& g, const Buffers& b, float* dst, cudaStream_t 
 void launch_field_out_t(const Geom& g, const Buffers& b, const Terms& T, const Stt& S, const float* m, int mode,
                         double freq, double phase, cudaStream_t s);
 void launch_normalize(const Geom& g, const Buffers& b, float* m, cudaStream_t s);
+// *flag = 1 if the 3 n floats of a and b differ in any bit (caller zeroes it)
+void launch_m_differs(const Geom& g, const float* a, const float* b, int* flag, cudaStream_t s);
 // cell codes from mask, region and the Msat table
 void launch_codes(const Geom& g, const Buffers& b, cudaStream_t s);
 // sets the launch attributes (dynamic shared memory) of the row-stage
