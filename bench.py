@@ -399,13 +399,22 @@ def run_surrogate(args, local_rank, steps=40):
     import torch
     from paper_1406_7635_gb300 import mm
     p = WORKLOADS["film_512x512x1"]()
-    net = mm.FNO(p.ny, p.nx, width=32, layers=4, modes_x=24, modes_y=24, max_batch=4, seed=1)
+    net = mm.FNO(p.ny, p.nx, width=32, layers=4, modes_x=24, modes_y=24, max_batch=4, seed=1, device=local_rank)
     ctx = mm.Context.from_problem(p, device=local_rank)
     t0 = time.perf_counter()
     loss = ctx.train_surrogate(net, p.msat[0], n_pairs=args.pairs, traj_len=16, steps_between=5,
                                field_max=50e-3, epochs=args.epochs, batch=4, lr=1e-3, seed=2)
     train_s = time.perf_counter() - t0
     ctx.close()
+    # one surrogate evaluation (S = 1), wall time per synchronised call
+    u = torch.randn(3 * p.ny * p.nx, device=f"cuda:{local_rank}") * 0.5
+    yfno = torch.empty_like(u)
+    for _ in range(3):
+        net.forward(u, yfno, 1)
+    ts = time.perf_counter()
+    for _ in range(20):
+        net.forward(u, yfno, 1)
+    fwd_ms = (time.perf_counter() - ts) / 20 * 1e3
 
     def timed(setup):
         c = mm.Context.from_problem(p, device=local_rank)
@@ -432,7 +441,7 @@ def run_surrogate(args, local_rank, steps=40):
     net.close()
     return {"workload": "film_512x512x1 (2 nm cells), FNO width 32, 4 layers, 24 modes per axis",
             "pairs": args.pairs, "epochs": args.epochs, "train_s": train_s, "final_train_loss": loss,
-            "steps": steps, "exact_cell_steps_per_s": v_exact,
+            "steps": steps, "forward_ms": fwd_ms, "exact_cell_steps_per_s": v_exact,
             "guarded_cell_steps_per_s": v_guard, "guarded_speedup": v_guard / v_exact,
             "guard": {k: st_guard[k] for k in ("checks", "fallbacks", "last_rel_err", "steps")},
             "unguarded_cell_steps_per_s": v_free, "unguarded_speedup": v_free / v_exact,

@@ -31,12 +31,20 @@
 namespace mm {
 namespace {
 
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_df(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
+}
+
 // ---------------------------------------------------------------------------
 // bfloat16 tensor-core GEMM: C[b] = alpha op(A[b]) op(B[b]) + beta C[b]
 // (+ bias[m]).  op(A)(m, k) = TA ? A[k lda + m] : A[m lda + k];
 // op(B)(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  Split-K (gridDim.z =
 // batch * splits) adds alpha * partial into C with atomics (C prepared by the
-// caller).  Block tile 64 x 64 x 32, four warps of 32 x 32.
+// caller), or, with sPart > 0, writes split s's partial to C + s sPart (the
+// consumer sums the slices in a fixed order: deterministic).  With act set,
+// the result is also written to act at the same offset, through the exact
+// GELU when act_gelu.  Block tile 64 x 64 x 32, four warps of 32 x 32.
 // ---------------------------------------------------------------------------
 struct GemmArgs {
   int M, N, K;
@@ -50,6 +58,9 @@ struct GemmArgs {
   const float* bias;   // per-row bias or null
   int splits;          // split-K factor
   int atomic;          // add alpha * product into C with atomics (C prepared by the caller)
+  long long sPart;     // > 0: split s writes its partial product to C + s sPart (no bias, beta 0)
+  float* act;          // optional second output: act_gelu ? GELU(C) : C
+  int act_gelu;
 };
 
 constexpr int BM = 64, BN = 64, BK = 32, APITCH = BK + 8;
@@ -66,7 +77,8 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
   const int batch = blockIdx.z / a.splits, split = blockIdx.z % a.splits;
   const float* __restrict__ A = a.A + batch * a.sA;
   const float* __restrict__ B = a.B + batch * a.sB;
-  float* __restrict__ Cm = a.C + batch * a.sC;
+  float* __restrict__ Cm = a.C + batch * a.sC + split * a.sPart;
+  float* __restrict__ Am = a.act ? a.act + batch * a.sC : nullptr;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kchunk = ((a.K + a.splits - 1) / a.splits + BK - 1) / BK * BK;
   const int kbeg = split * kchunk, kend = min(a.K, kbeg + kchunk);
@@ -167,7 +179,8 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
         const int row = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
         const int col = n0 + wn + 8 * j + 2 * t + (r & 1);
         if (row >= a.M || col >= a.N) continue;
-        float* dst = Cm + (long long)row * a.ldc + col;
+        const long long o = (long long)row * a.ldc + col;
+        float* dst = Cm + o;
         const float v = a.alpha * acc[i][j][r];
         if (a.atomic) {
           atomicAdd(dst, v);
@@ -175,6 +188,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
           float out = v + (a.bias ? a.bias[row] : 0.f);
           if (a.beta != 0.f) out += a.beta * *dst;
           *dst = out;
+          if (Am) Am[o] = a.act_gelu ? gelu_f(out) : out;
         }
       }
 }
@@ -190,7 +204,23 @@ void gemm(cudaStream_t s, bool ta, bool tb, int batch, const GemmArgs& a) {
 GemmArgs gargs(int M, int N, int K, const float* A, long long lda, long long sA, const float* B, long long ldb,
                long long sB, float* C, long long ldc, long long sC, float alpha = 1.f, float beta = 0.f,
                const float* bias = nullptr, int splits = 1, int atomic = 0) {
-  return GemmArgs{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, beta, bias, splits, atomic || splits > 1};
+  return GemmArgs{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, beta, bias, splits, atomic || splits > 1,
+                  0, nullptr, 0};
+}
+
+// split-K into `parts` slices part_stride floats apart (see GemmArgs::sPart)
+GemmArgs sliced(GemmArgs a, int parts, long long part_stride) {
+  a.splits = parts;
+  a.atomic = 0;
+  a.sPart = part_stride;
+  return a;
+}
+
+// second output through GELU (gelu) or as is
+GemmArgs with_act(GemmArgs a, float* act, bool gelu) {
+  a.act = act;
+  a.act_gelu = gelu ? 1 : 0;
+  return a;
 }
 
 // ---------------------------------------------------------------------------
@@ -246,6 +276,296 @@ __global__ void k_yexpand(int S, int C, int H, int J, int Mx, const float2* __re
   row[Mx + k] = im;
 }
 
+// The same two products tiled through shared memory (one block per sample and
+// channel and group of frequencies, or of rows): the one-thread-per-output
+// kernels above walk a whole column of global memory per thread, which is
+// latency-bound.  Same summation order per output (y, resp. j, ascending).
+constexpr int kYNT = 256;
+constexpr int kXParts = 4;   // most split-K slices of the x partial DFT products
+constexpr int kYSplit = 8;   // most row ranges of the tiled y product
+
+// as k_ysum; blocked X may be split-K partials: the sum of `parts` slices
+// part_stride floats apart (slice 0 first).  Block (j group, sc, row range):
+// JB frequencies x Mx columns over rows [z YR, (z + 1) YR), staged YC rows
+// at a time; range z writes its partial sums to Y + z y_stride (one range:
+// the result itself).
+__global__ void __launch_bounds__(kYNT) k_ysum_t(int H, int J, int Mx, int JB, int YC, int YR,
+                                               const float* __restrict__ X, bool x_blocked, int parts,
+                                               long long part_stride, const float2* __restrict__ F, bool conj_f,
+                                               float2* __restrict__ Y, long long y_stride) {
+  extern __shared__ float2 ysh[];
+  float2* xs = ysh;             // [YC][Mx]
+  float2* fs = ysh + YC * Mx;   // [JB][YC]
+  const long long sc = blockIdx.y;
+  const int j0 = blockIdx.x * JB, jn = min(JB, J - j0);
+  const int tid = threadIdx.x, jj = tid / Mx, k = tid % Mx;
+  const bool mine = jj < jn;
+  float re = 0.f, im = 0.f;
+  const int ybeg = blockIdx.z * YR, yend = min(H, ybeg + YR);
+  Y += blockIdx.z * y_stride;
+  for (int y0 = ybeg; y0 < yend; y0 += YC) {
+    const int yn = min(YC, yend - y0);
+    for (int e = tid; e < yn * Mx; e += kYNT) {
+      const int yy = e / Mx, kk = e % Mx;
+      const long long ri = sc * H + y0 + yy;
+      float2 v;
+      if (x_blocked) {
+        const float* row = X + ri * 2 * Mx;
+        v = make_float2(row[kk], row[Mx + kk]);
+        for (int q = 1; q < parts; ++q) {
+          v.x += row[q * part_stride + kk];
+          v.y += row[q * part_stride + Mx + kk];
+        }
+      } else {
+        v = reinterpret_cast<const float2*>(X)[ri * Mx + kk];
+      }
+      xs[yy * Mx + kk] = v;
+    }
+    for (int e = tid; e < jn * yn; e += kYNT) {
+      const int a = e / yn, yy = e % yn;
+      float2 f = F[(long long)(j0 + a) * H + y0 + yy];
+      if (conj_f) f.y = -f.y;
+      fs[a * YC + yy] = f;
+    }
+    __syncthreads();
+    if (mine) {
+      for (int yy = 0; yy < yn; ++yy) {
+        const float2 f = fs[jj * YC + yy], x = xs[yy * Mx + k];
+        re = fmaf(f.x, x.x, fmaf(-f.y, x.y, re));
+        im = fmaf(f.x, x.y, fmaf(f.y, x.x, im));
+      }
+    }
+    __syncthreads();
+  }
+  if (mine) Y[(sc * J + j0 + jj) * Mx + k] = make_float2(re, im);
+}
+
+// dst[i] = sum_z src[z stride + i] over z < parts (ascending)
+__global__ void k_sum_parts(long long n, int parts, long long stride, const float2* __restrict__ src,
+                            float2* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float2 a = src[i];
+  for (int z = 1; z < parts; ++z) {
+    const float2 b = src[z * stride + i];
+    a.x += b.x;
+    a.y += b.y;
+  }
+  dst[i] = a;
+}
+
+// as k_yexpand; block (row group, sc): O[sc] (J x Mx) and F[:, y0 .. y0+YB)
+// staged, YB x Mx outputs
+__global__ void __launch_bounds__(kYNT) k_yexpand_t(int H, int J, int Mx, int YB, const float2* __restrict__ O,
+                                                  const float2* __restrict__ F, bool conj_f, float* __restrict__ Z) {
+  extern __shared__ float2 ysh[];
+  float2* os = ysh;             // [J][Mx]
+  float2* fs = ysh + J * Mx;    // [J][YB]
+  const long long sc = blockIdx.y;
+  const int y0 = blockIdx.x * YB, yn = min(YB, H - y0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < J * Mx; e += kYNT) os[e] = O[sc * J * Mx + e];
+  for (int e = tid; e < J * yn; e += kYNT) {
+    const int j = e / yn, yy = e % yn;
+    float2 f = F[(long long)j * H + y0 + yy];
+    if (conj_f) f.y = -f.y;
+    fs[j * YB + yy] = f;
+  }
+  __syncthreads();
+  for (int e = tid; e < yn * Mx; e += kYNT) {
+    const int yy = e / Mx, k = e % Mx;
+    float re = 0.f, im = 0.f;
+    for (int j = 0; j < J; ++j) {
+      const float2 f = fs[j * YB + yy], o = os[j * Mx + k];
+      re = fmaf(f.x, o.x, fmaf(-f.y, o.y, re));
+      im = fmaf(f.x, o.y, fmaf(f.y, o.x, im));
+    }
+    float* row = Z + (sc * H + y0 + yy) * 2 * Mx;
+    row[k] = re;
+    row[Mx + k] = im;
+  }
+}
+
+// tile shapes of the two (shared memory <= 48 KB)
+struct YTile {
+  int JB, YC;   // ysum: frequencies per block, rows per stage
+  int YB;       // yexpand: rows per block (0: untiled kernel)
+  bool ysum;    // ysum tiled
+  int ysplit;   // ysum: row ranges (partials summed by k_sum_parts)
+};
+YTile ytile(int S, int C, int H, int J, int Mx, int sms) {
+  YTile t{};
+  t.ysum = Mx <= kYNT && (long long)S * C <= 65535;
+  t.ysplit = 1;
+  if (t.ysum) {
+    t.JB = std::min(J, std::min(64, kYNT / Mx));
+    t.YC = std::max(1, std::min(64, 2048 / Mx));
+    // row ranges until about four blocks per multiprocessor, at least a stage each
+    const long long blocks = (long long)((J + t.JB - 1) / t.JB) * S * C;
+    const long long want = (4LL * sms + blocks - 1) / blocks;
+    t.ysplit = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(want, kYSplit),
+                                                                 (H + t.YC - 1) / t.YC));
+  }
+  t.YB = 0;
+  if ((long long)S * C <= 65535 && J * Mx <= 4096) {
+    const int yb = (6144 - J * Mx) / J;   // (J Mx + J YB) float2 <= 48 KB
+    t.YB = std::min(H, std::min(64, yb));
+    if (t.YB < 1) t.YB = 0;
+  }
+  return t;
+}
+
+// (Yp: kYSplit S C J Mx float2 of scratch for the row-range partials)
+void ysum(cudaStream_t s, const YTile& t, int S, int C, int H, int J, int Mx, const float* X, bool blocked, int parts,
+          long long part_stride, const float2* F, bool conj_f, float2* Y, float2* Yp) {
+  if (!t.ysum) {   // (parts == 1 here: sliced products are only made for the tiled kernel)
+    k_ysum<<<(unsigned)(((long long)S * C * J * Mx + 255) / 256), 256, 0, s>>>(S, C, H, J, Mx, X, blocked, F, conj_f, Y);
+    return;
+  }
+  const int YR = (H + t.ysplit - 1) / t.ysplit;
+  const dim3 grid((J + t.JB - 1) / t.JB, S * C, t.ysplit);
+  const size_t smem = (size_t)(t.YC * Mx + t.JB * t.YC) * sizeof(float2);
+  const long long n = (long long)S * C * J * Mx;
+  k_ysum_t<<<grid, kYNT, smem, s>>>(H, J, Mx, t.JB, t.YC, YR, X, blocked, parts, part_stride, F, conj_f,
+                                    t.ysplit > 1 ? Yp : Y, n);
+  if (t.ysplit > 1) k_sum_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, t.ysplit, n, Yp, Y);
+}
+
+void yexpand(cudaStream_t s, const YTile& t, int S, int C, int H, int J, int Mx, const float2* O, const float2* F,
+             bool conj_f, float* Z) {
+  if (t.YB == 0) {
+    k_yexpand<<<(unsigned)(((long long)S * C * H * Mx + 255) / 256), 256, 0, s>>>(S, C, H, J, Mx, O, F, conj_f, Z);
+    return;
+  }
+  const dim3 grid((H + t.YB - 1) / t.YB, S * C);
+  const size_t smem = (size_t)(J * Mx + J * t.YB) * sizeof(float2);
+  k_yexpand_t<<<grid, kYNT, smem, s>>>(H, J, Mx, t.YB, O, F, conj_f, Z);
+}
+
+// Pointwise channel products on the FP32 cores, one thread per pixel (these
+// are memory-bound: a tensor-core GEMM with M = C rows leaves most of its
+// tile idle and needs a second pass for the activation):
+//   out[s][o][p] = bias[o] + (SPEC: sum_k Zb[s][o][y][k] G[k][x]) + sum_i A[o][i] in[s][i][p]
+// with p = y W + x; ACT 1 also writes GELU(out) to act, ACT 2 a copy.  The
+// spectral part is the inverse x partial DFT of the layer (Zb blocked
+// [re Mx | im Mx] rows, G = Gblk).  A block is kPwNT pixels of one image
+// row; it stages A, that row of Zb (as [i][o] and [k][o]: pitch a multiple of
+// 4 plus 4 floats, aligned float4 reads) and its columns of G ([k][pixel])
+// in shared memory with asynchronous copies, all in flight together.
+constexpr int kPwNT = 128;
+__host__ __device__ constexpr int pw_pitch(int co) { return (co + 3) / 4 * 4 + 4; }
+
+// 4-byte asynchronous global -> shared copy (completes at cp.async.wait_all)
+__device__ __forceinline__ void cp_async_4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+template <int CI, int CO, bool SPEC, int ACT>
+__global__ void __launch_bounds__(kPwNT) k_pointwise(int H, int W, int K2, const float* __restrict__ A,
+                                                   const float* __restrict__ bias, const float* __restrict__ in,
+                                                   const float* __restrict__ Zb, const float* __restrict__ G,
+                                                   float* __restrict__ out, float* __restrict__ act) {
+  constexpr int P = pw_pitch(CO);
+  extern __shared__ __align__(16) float pws[];
+  float* As = pws;                  // [CI][P]
+  float* Zs = pws + CI * P;         // [K2][P]
+  float* Gs = Zs + K2 * P;          // [K2][kPwNT]
+  const int x0 = blockIdx.x * kPwNT, x = x0 + threadIdx.x, y = blockIdx.y, s = blockIdx.z;
+  for (int e = threadIdx.x; e < CI * CO; e += kPwNT) cp_async_4(&As[(e % CI) * P + e / CI], &A[e]);
+  if (SPEC) {
+    const float* zrow = Zb + ((long long)s * CO * H + y) * K2;   // + o H K2 + k
+    for (int e = threadIdx.x; e < K2 * CO; e += kPwNT) {
+      const int o = e / K2, k = e % K2;
+      cp_async_4(&Zs[k * P + o], &zrow[(long long)o * H * K2 + k]);
+    }
+    if (x < W)
+      for (int k = 0; k < K2; ++k) cp_async_4(&Gs[k * kPwNT + threadIdx.x], &G[(long long)k * W + x]);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  if (x >= W) return;
+  const long long N = (long long)H * W, px = (long long)y * W + x;
+  float vi[CI];
+#pragma unroll
+  for (int i = 0; i < CI; ++i) vi[i] = in[((long long)s * CI + i) * N + px];
+  float acc[CO];
+#pragma unroll
+  for (int o = 0; o < CO; ++o) acc[o] = __ldg(&bias[o]);
+  if (SPEC) {
+#pragma unroll 4
+    for (int k = 0; k < K2; ++k) {
+      const float g = Gs[k * kPwNT + threadIdx.x];
+      const float* zr = Zs + k * P;
+#pragma unroll
+      for (int o = 0; o < CO; o += 4) {
+        const float4 z4 = *reinterpret_cast<const float4*>(zr + o);
+        acc[o] = fmaf(z4.x, g, acc[o]);
+        if (o + 1 < CO) acc[o + 1] = fmaf(z4.y, g, acc[o + 1]);
+        if (o + 2 < CO) acc[o + 2] = fmaf(z4.z, g, acc[o + 2]);
+        if (o + 3 < CO) acc[o + 3] = fmaf(z4.w, g, acc[o + 3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < CI; ++i) {
+    const float* ar = As + i * P;
+#pragma unroll
+    for (int o = 0; o < CO; o += 4) {
+      const float4 a4 = *reinterpret_cast<const float4*>(ar + o);
+      acc[o] = fmaf(a4.x, vi[i], acc[o]);
+      if (o + 1 < CO) acc[o + 1] = fmaf(a4.y, vi[i], acc[o + 1]);
+      if (o + 2 < CO) acc[o + 2] = fmaf(a4.z, vi[i], acc[o + 2]);
+      if (o + 3 < CO) acc[o + 3] = fmaf(a4.w, vi[i], acc[o + 3]);
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < CO; ++o) {
+    const long long oi = ((long long)s * CO + o) * N + px;
+    out[oi] = acc[o];
+    if (ACT == 1) act[oi] = gelu_f(acc[o]);
+    if (ACT == 2) act[oi] = acc[o];
+  }
+}
+
+template <int CI, int CO, bool SPEC, int ACT>
+void launch_pw(cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias, const float* in,
+               const float* Zb, const float* G, float* out, float* act) {
+  const size_t smem = ((size_t)(CI + (SPEC ? K2 : 0)) * pw_pitch(CO) + (SPEC ? (size_t)K2 * kPwNT : 0)) * sizeof(float);
+  const dim3 grid((W + kPwNT - 1) / kPwNT, H, S);
+  k_pointwise<CI, CO, SPEC, ACT><<<grid, kPwNT, smem, s>>>(H, W, K2, A, bias, in, Zb, G, out, act);
+}
+
+// the layer output (CI = CO = C, spectral part, act 1 GELU / 2 copy), the lift
+// (CI = 3) and the projection (CO = 3) for C in {4, 8, 16, 32}; false where
+// there is no instantiation or the staged tables exceed 48 KB (the caller
+// then takes the GEMM path)
+enum PwKind { kPwLayer, kPwLift, kPwProject };
+template <int C>
+bool pw_c(PwKind kind, cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias,
+          const float* in, const float* Zb, const float* G, float* out, float* act, int act_kind) {
+  if (kind == kPwLift) launch_pw<3, C, false, 0>(s, S, H, W, 0, A, bias, in, nullptr, nullptr, out, nullptr);
+  else if (kind == kPwProject) launch_pw<C, 3, false, 0>(s, S, H, W, 0, A, bias, in, nullptr, nullptr, out, nullptr);
+  else if (act_kind == 1) launch_pw<C, C, true, 1>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
+  else launch_pw<C, C, true, 2>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
+  return true;
+}
+bool pointwise(PwKind kind, cudaStream_t s, int S, int C, int H, int W, int K2, const float* A, const float* bias,
+               const float* in, const float* Zb, const float* G, float* out, float* act, int act_kind) {
+  if (H > 65535 || S > 65535) return false;
+  const int ci = kind == kPwLift ? 3 : C, co = kind == kPwProject ? 3 : C;
+  if (((long long)(ci + (kind == kPwLayer ? K2 : 0)) * pw_pitch(co) + (kind == kPwLayer ? (long long)K2 * kPwNT : 0)) *
+          4 > 49152)
+    return false;
+  switch (C) {
+    case 4: return pw_c<4>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
+    case 8: return pw_c<8>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
+    case 16: return pw_c<16>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
+    case 32: return pw_c<32>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
+    default: return false;
+  }
+}
+
 // O[s][o][m] = sum_i R[o][i][m] V[s][i][m]   (conj: sum_o conj(R[o][i][m]) V[s][o][m] -> O[s][i][m])
 __global__ void k_mix(int S, int C, int NM, const float2* __restrict__ R, const float2* __restrict__ V,
                       float2* __restrict__ O, bool adjoint) {
@@ -255,6 +575,7 @@ __global__ void k_mix(int S, int C, int NM, const float2* __restrict__ R, const 
   const int m = (int)(idx % NM), o = (int)((idx / NM) % C);
   const long long s = idx / ((long long)NM * C);
   float re = 0.f, im = 0.f;
+#pragma unroll 8
   for (int i = 0; i < C; ++i) {
     float2 r = adjoint ? R[((long long)i * C + o) * NM + m] : R[((long long)o * C + i) * NM + m];
     if (adjoint) r.y = -r.y;
@@ -283,15 +604,6 @@ __global__ void k_dR(int S, int C, int NM, const float2* __restrict__ dO, const 
   dR[idx].y += im;
 }
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_df(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
-}
-
-__global__ void k_gelu(long long n, const float* __restrict__ z, float* __restrict__ v) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = gelu_f(z[i]);
-}
 __global__ void k_gelu_back(long long n, const float* __restrict__ z, float* __restrict__ dv) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dv[i] *= gelu_df(z[i]);
@@ -396,7 +708,9 @@ struct mm_fno {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int C = 0, L = 0, Mx = 0, My = 0, H = 0, W = 0, J = 0, Smax = 0;
+  int sms = 1;                  // multiprocessors of the device
   long long N = 0, nparam = 0;
+  long long xslice = 0;         // floats between the split-K slices of X and Z
   std::vector<long long> off;   // P, p, {W, b, R} per layer, Q, q
   float *prm = nullptr, *grd = nullptr, *m1 = nullptr, *m2 = nullptr;
   long long adam_t = 0;
@@ -409,6 +723,7 @@ struct mm_fno {
   std::vector<float2*> V;                   // L
   float *X = nullptr, *Z = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr;
   float2 *O = nullptr, *dO = nullptr, *dV = nullptr;
+  float2* Yp = nullptr;                     // row-range partials of the y product
   double* acc = nullptr;
 };
 
@@ -434,6 +749,18 @@ int sW(int l) { return 2 + 3 * l; }
 int sb(int l) { return 3 + 3 * l; }
 int sR(int l) { return 4 + 3 * l; }
 
+// Slices of the x partial DFT products (M = C H rows, N = 2 Mx, K = W): split
+// K until there are about four blocks per multiprocessor; the tiled y
+// product sums the slices.
+int xparts(const mm_fno* f, int S, const YTile& t) {
+  if (!t.ysum) return 1;
+  const long long blocks = (long long)((2 * f->Mx + BN - 1) / BN) * ((f->C * f->H + BM - 1) / BM) * S;
+  long long p = (4LL * f->sms + blocks - 1) / blocks;
+  p = std::min<long long>(p, kXParts);
+  p = std::min<long long>(p, (f->W + BK - 1) / BK);
+  return (int)std::max<long long>(1, p);
+}
+
 // forward for S samples whose inputs are already in f->u; output in f->yh
 void fwd(mm_fno* f, int S) {
   cudaStream_t s = f->stream;
@@ -441,27 +768,33 @@ void fwd(mm_fno* f, int S) {
   const long long N = f->N, CN = (long long)C * N;
   const int L = f->L;
   const int q = sW(L) , qq = sb(L);
+  const YTile yt = ytile(S, C, H, J, Mx, f->sms);
+  const int xp = xparts(f, S, yt);
   // lift: v0[C x N] = P[C x 3] u[3 x N] + p
-  gemm(s, false, false, S, gargs(C, (int)N, 3, P_(f, 0), 3, 0, f->u, N, 3 * N, f->v[0], N, CN, 1.f, 0.f, P_(f, 1)));
+  if (!pointwise(kPwLift, s, S, C, H, W, 0, P_(f, 0), P_(f, 1), f->u, nullptr, nullptr, f->v[0], nullptr, 0))
+    gemm(s, false, false, S, gargs(C, (int)N, 3, P_(f, 0), 3, 0, f->u, N, 3 * N, f->v[0], N, CN, 1.f, 0.f, P_(f, 1)));
   for (int l = 0; l < L; ++l) {
     float* vin = f->v[l];
     // X = v [C H x W] . Fblk [W x 2Mx]
-    gemm(s, false, false, S, gargs(C * H, 2 * Mx, W, vin, W, CN, f->Fblk, 2 * Mx, 0, f->X, 2 * Mx,
-                                   (long long)C * H * 2 * Mx));
-    k_ysum<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->X, true, f->Fy, false, f->V[l]);
+    gemm(s, false, false, S, sliced(gargs(C * H, 2 * Mx, W, vin, W, CN, f->Fblk, 2 * Mx, 0, f->X, 2 * Mx,
+                                          (long long)C * H * 2 * Mx), xp, f->xslice));
+    ysum(s, yt, S, C, H, J, Mx, f->X, true, xp, f->xslice, f->Fy, false, f->V[l], f->Yp);
     k_mix<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
                                                       f->V[l], f->O, false);
-    k_yexpand<<<nb((long long)S * C * H * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->O, f->Gy, false, f->Z);
-    // z = Z_blk [C H x 2Mx] . Gblk [2Mx x W]  (spectral part), then += W v + b
-    gemm(s, false, false, S, gargs(C * H, W, 2 * Mx, f->Z, 2 * Mx, (long long)C * H * 2 * Mx, f->Gblk, W, 0, f->z[l],
-                                   W, CN));
-    gemm(s, false, false, S, gargs(C, (int)N, C, P_(f, sW(l)), C, 0, vin, N, CN, f->z[l], N, CN, 1.f, 1.f,
-                                   P_(f, sb(l))));
-    if (l < L - 1) k_gelu<<<nb(S * CN), 256, 0, s>>>(S * CN, f->z[l], f->v[l + 1]);
-    else cudaMemcpyAsync(f->v[l + 1], f->z[l], S * CN * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    yexpand(s, yt, S, C, H, J, Mx, f->O, f->Gy, false, f->Z);
+    // z = Z_blk [C H x 2Mx] . Gblk [2Mx x W] (spectral part) + W v + b, and
+    // v_{l+1} = GELU(z) (z after the last layer)
+    if (!pointwise(kPwLayer, s, S, C, H, W, 2 * Mx, P_(f, sW(l)), P_(f, sb(l)), vin, f->Z, f->Gblk, f->z[l],
+                   f->v[l + 1], l < L - 1 ? 1 : 2)) {
+      gemm(s, false, false, S, gargs(C * H, W, 2 * Mx, f->Z, 2 * Mx, (long long)C * H * 2 * Mx, f->Gblk, W, 0,
+                                     f->z[l], W, CN));
+      gemm(s, false, false, S, with_act(gargs(C, (int)N, C, P_(f, sW(l)), C, 0, vin, N, CN, f->z[l], N, CN, 1.f, 1.f,
+                                              P_(f, sb(l))), f->v[l + 1], l < L - 1));
+    }
   }
   // project: y[3 x N] = Q[3 x C] v_L + q
-  gemm(s, false, false, S, gargs(3, (int)N, C, P_(f, q), C, 0, f->v[L], N, CN, f->yh, N, 3 * N, 1.f, 0.f, P_(f, qq)));
+  if (!pointwise(kPwProject, s, S, C, H, W, 0, P_(f, q), P_(f, qq), f->v[L], nullptr, nullptr, f->yh, nullptr, 0))
+    gemm(s, false, false, S, gargs(3, (int)N, C, P_(f, q), C, 0, f->v[L], N, CN, f->yh, N, 3 * N, 1.f, 0.f, P_(f, qq)));
 }
 
 // gradients of the batch loss into f->grd (zeroed here); loss pieces in acc
@@ -470,6 +803,8 @@ void bwd(mm_fno* f, int S, const float* y) {
   const int C = f->C, H = f->H, W = f->W, Mx = f->Mx, J = f->J, L = f->L;
   const long long N = f->N, CN = (long long)C * N;
   const int splits = (int)std::min<long long>(64, std::max<long long>(1, N / 4096));
+  const YTile yt = ytile(S, C, H, J, Mx, f->sms);
+  const int xp = xparts(f, S, yt);
   cudaMemsetAsync(f->grd, 0, f->nparam * sizeof(float), s);
   cudaMemsetAsync(f->acc, 0, 2 * sizeof(double), s);
   k_loss<<<1024, 256, 0, s>>>(S * 3 * N, f->yh, y, f->acc);
@@ -490,13 +825,14 @@ void bwd(mm_fno* f, int S, const float* y) {
     // dv2 = W^T dz
     gemm(s, true, false, S, gargs(C, (int)N, C, P_(f, sW(l)), C, 0, dzl, N, CN, f->dv2, N, CN));
     // spectral adjoint: dZ_blk = dz [C H x W] . Gblk^T
-    gemm(s, false, true, S, gargs(C * H, 2 * Mx, W, dzl, W, CN, f->Gblk, W, 0, f->Z, 2 * Mx, (long long)C * H * 2 * Mx));
-    k_ysum<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->Z, true, f->Gy, true, f->dO);
+    gemm(s, false, true, S, sliced(gargs(C * H, 2 * Mx, W, dzl, W, CN, f->Gblk, W, 0, f->Z, 2 * Mx,
+                                         (long long)C * H * 2 * Mx), xp, f->xslice));
+    ysum(s, yt, S, C, H, J, Mx, f->Z, true, xp, f->xslice, f->Gy, true, f->dO, f->Yp);
     k_dR<<<nb((long long)C * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, f->dO, f->V[l],
                                                       reinterpret_cast<float2*>(G_(f, sR(l))));
     k_mix<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
                                                       f->dO, f->dV, true);
-    k_yexpand<<<nb((long long)S * C * H * Mx), 256, 0, s>>>(S, C, H, J, Mx, f->dV, f->Fy, true, f->X);
+    yexpand(s, yt, S, C, H, J, Mx, f->dV, f->Fy, true, f->X);
     // dv2 += dX_blk [C H x 2Mx] . Fblk^T [2Mx x W]
     gemm(s, false, true, S, gargs(C * H, W, 2 * Mx, f->X, 2 * Mx, (long long)C * H * 2 * Mx, f->Fblk, 2 * Mx, 0, f->dv2,
                                   W, CN, 1.f, 1.f));
@@ -520,8 +856,11 @@ int mm_fno_create(mm_fno** out, int H, int W, const mm_fno_cfg* cfg, int device,
   if (H < 2 || W < 2 || C < 1 || L < 1 || Mx < 1 || My < 1 || Smax < 1 || Mx > W / 2 || 2 * My > H)
     return ffail(MM_ERR_ARG, "need H, W >= 2, width, layers, batch >= 1, modes_x <= W/2, 2 modes_y <= H");
   MMF_CUDA(cudaSetDevice(device));
+  int sms = 1;
+  MMF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   mm_fno* f = new mm_fno();
   f->device = device;
+  f->sms = sms;
   f->C = C; f->L = L; f->Mx = Mx; f->My = My; f->H = H; f->W = W; f->J = 2 * My; f->Smax = Smax;
   f->N = (long long)H * W;
   auto cleanup = [&](int code) { mm_fno_destroy(f); return code; };
@@ -563,13 +902,15 @@ int mm_fno_create(mm_fno** out, int H, int W, const mm_fno_cfg* cfg, int device,
   for (int l = 0; l <= L; ++l) alloc((void**)&f->v[l], (size_t)Smax * CN * sizeof(float));
   for (int l = 0; l < L; ++l) alloc((void**)&f->z[l], (size_t)Smax * CN * sizeof(float));
   for (int l = 0; l < L; ++l) alloc((void**)&f->V[l], (size_t)Smax * C * f->J * Mx * sizeof(float2));
-  alloc((void**)&f->X, (size_t)Smax * C * H * 2 * Mx * sizeof(float));
-  alloc((void**)&f->Z, (size_t)Smax * C * H * 2 * Mx * sizeof(float));
+  f->xslice = (long long)Smax * C * H * 2 * Mx;
+  alloc((void**)&f->X, (size_t)kXParts * f->xslice * sizeof(float));
+  alloc((void**)&f->Z, (size_t)kXParts * f->xslice * sizeof(float));
   alloc((void**)&f->dv, (size_t)Smax * CN * sizeof(float));
   alloc((void**)&f->dv2, (size_t)Smax * CN * sizeof(float));
   alloc((void**)&f->O, (size_t)Smax * C * f->J * Mx * sizeof(float2));
   alloc((void**)&f->dO, (size_t)Smax * C * f->J * Mx * sizeof(float2));
   alloc((void**)&f->dV, (size_t)Smax * C * f->J * Mx * sizeof(float2));
+  alloc((void**)&f->Yp, (size_t)kYSplit * Smax * C * f->J * Mx * sizeof(float2));
   alloc((void**)&f->acc, 4 * sizeof(double));
   if (e != cudaSuccess) return cleanup(ffail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, cudaGetErrorString(e)));
   // partial DFT matrices (float64 on the host, rounded once)
@@ -630,7 +971,7 @@ int mm_fno_destroy(mm_fno* f) {
   cudaSetDevice(f->device);
   if (f->stream) cudaStreamSynchronize(f->stream);
   void* ptrs[] = {f->prm, f->grd, f->m1, f->m2, f->Fblk, f->Gblk, f->Fy, f->Gy, f->u, f->yh, f->dy,
-                  f->X, f->Z, f->dv, f->dv2, f->O, f->dO, f->dV, f->acc};
+                  f->X, f->Z, f->dv, f->dv2, f->O, f->dO, f->dV, f->Yp, f->acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (float* p : f->v) if (p) cudaFree(p);
