@@ -93,53 +93,83 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
 
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    // stage A (BM x BK) and B (BN x BK), k contiguous in shared memory
-#pragma unroll 4
-    for (int e = tid; e < BM * BK / 2; e += 128) {
+  // operand pairs of one BK step in registers: the next step's global loads
+  // are in flight while the tensor cores work on the current one
+  constexpr int PA = BM * BK / 2 / 128, PB = BN * BK / 2 / 128;
+  float ra[PA][2], rb[PB][2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < PA; ++u) {
+      const int e = tid + u * 128;
       int mm_, kk;
       if (TA) { mm_ = (2 * e) % BM; kk = (2 * e) / BM; } else { mm_ = (2 * e) / BK; kk = (2 * e) % BK; }
+      const int gm = m0 + mm_, gk = k0 + kk;
       float v0 = 0.f, v1 = 0.f;
       if (TA) {
-        const int gm = m0 + mm_, gk = k0 + kk;
         if (gk < kend) {
           if (gm < a.M) v0 = A[(long long)gk * a.lda + gm];
           if (gm + 1 < a.M) v1 = A[(long long)gk * a.lda + gm + 1];
         }
-        As[mm_][kk] = __float2bfloat16_rn(v0);
-        As[mm_ + 1][kk] = __float2bfloat16_rn(v1);
-      } else {
-        const int gm = m0 + mm_, gk = k0 + kk;
-        if (gm < a.M) {
-          if (gk < kend) v0 = A[(long long)gm * a.lda + gk];
-          if (gk + 1 < kend) v1 = A[(long long)gm * a.lda + gk + 1];
-        }
-        *reinterpret_cast<unsigned*>(&As[mm_][kk]) = pack_bf16(v0, v1);
+      } else if (gm < a.M) {
+        if (gk < kend) v0 = A[(long long)gm * a.lda + gk];
+        if (gk + 1 < kend) v1 = A[(long long)gm * a.lda + gk + 1];
       }
+      ra[u][0] = v0;
+      ra[u][1] = v1;
     }
-#pragma unroll 4
-    for (int e = tid; e < BN * BK / 2; e += 128) {
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int e = tid + u * 128;
       int nn, kk;
       if (TB) { nn = (2 * e) / BK; kk = (2 * e) % BK; } else { nn = (2 * e) % BN; kk = (2 * e) / BN; }
+      const int gn = n0 + nn, gk = k0 + kk;
       float v0 = 0.f, v1 = 0.f;
       if (TB) {
-        const int gn = n0 + nn, gk = k0 + kk;
         if (gn < a.N) {
           if (gk < kend) v0 = B[(long long)gn * a.ldb + gk];
           if (gk + 1 < kend) v1 = B[(long long)gn * a.ldb + gk + 1];
         }
-        *reinterpret_cast<unsigned*>(&Bs[nn][kk]) = pack_bf16(v0, v1);
+      } else if (gk < kend) {
+        if (gn < a.N) v0 = B[(long long)gk * a.ldb + gn];
+        if (gn + 1 < a.N) v1 = B[(long long)gk * a.ldb + gn + 1];
+      }
+      rb[u][0] = v0;
+      rb[u][1] = v1;
+    }
+  };
+  // stage A (BM x BK) and B (BN x BK), k contiguous in shared memory
+  auto store = [&]() {
+#pragma unroll
+    for (int u = 0; u < PA; ++u) {
+      const int e = tid + u * 128;
+      if (TA) {
+        const int mm_ = (2 * e) % BM, kk = (2 * e) / BM;
+        As[mm_][kk] = __float2bfloat16_rn(ra[u][0]);
+        As[mm_ + 1][kk] = __float2bfloat16_rn(ra[u][1]);
       } else {
-        const int gn = n0 + nn, gk = k0 + kk;
-        if (gk < kend) {
-          if (gn < a.N) v0 = B[(long long)gk * a.ldb + gn];
-          if (gn + 1 < a.N) v1 = B[(long long)gk * a.ldb + gn + 1];
-        }
-        Bs[nn][kk] = __float2bfloat16_rn(v0);
-        Bs[nn + 1][kk] = __float2bfloat16_rn(v1);
+        const int mm_ = (2 * e) / BK, kk = (2 * e) % BK;
+        *reinterpret_cast<unsigned*>(&As[mm_][kk]) = pack_bf16(ra[u][0], ra[u][1]);
       }
     }
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int e = tid + u * 128;
+      if (TB) {
+        const int nn = (2 * e) / BK, kk = (2 * e) % BK;
+        *reinterpret_cast<unsigned*>(&Bs[nn][kk]) = pack_bf16(rb[u][0], rb[u][1]);
+      } else {
+        const int nn = (2 * e) % BN, kk = (2 * e) / BN;
+        Bs[nn][kk] = __float2bfloat16_rn(rb[u][0]);
+        Bs[nn + 1][kk] = __float2bfloat16_rn(rb[u][1]);
+      }
+    }
+  };
+
+  if (kbeg < kend) load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    store();
     __syncthreads();
+    if (k0 + BK < kend) load(k0 + BK);
 #pragma unroll
     for (int ks = 0; ks < BK; ks += 16) {
       unsigned af[2][4], bfr[4][2];
@@ -455,10 +485,15 @@ void yexpand(cudaStream_t s, const YTile& t, int S, int C, int H, int J, int Mx,
 constexpr int kPwNT = 128;
 __host__ __device__ constexpr int pw_pitch(int co) { return (co + 3) / 4 * 4 + 4; }
 
-// 4-byte asynchronous global -> shared copy (completes at cp.async.wait_all)
+// 4- and 16-byte asynchronous global -> shared copies (complete at
+// cp.async.wait_all; the 16-byte form needs both addresses 16-byte aligned)
 __device__ __forceinline__ void cp_async_4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
 template <int CI, int CO, bool SPEC, int ACT>
@@ -528,6 +563,147 @@ __global__ void __launch_bounds__(kPwNT) k_pointwise(int H, int W, int K2, const
   }
 }
 
+// The layer output for C a multiple of 8, register-blocked: thread (g, q)
+// computes channels 8g .. 8g + 7 at pixels 4q .. 4q + 3 of the block's
+// kPwNT pixels (C / 8 warps; channel group uniform per warp), so one float4
+// of Zs / A (broadcast) and one of G / v feed 32 FMAs.  A, Zb's row, G's
+// columns and v's pixels are staged with asynchronous copies; with W a
+// multiple of 4 (every row and pixel quad 16-byte aligned) G and v move in
+// 16-byte copies and the outputs in float4 stores.
+template <int C, int ACT>
+__global__ void __launch_bounds__(C * 4) k_layer_pw(int H, int W, int K2, const float* __restrict__ A,
+                                                   const float* __restrict__ bias, const float* __restrict__ in,
+                                                   const float* __restrict__ Zb, const float* __restrict__ G,
+                                                   float* __restrict__ out, float* __restrict__ act) {
+  constexpr int NT = C * 4, P = pw_pitch(C);
+  static_assert(C % 8 == 0, "channel groups of 8");
+  extern __shared__ __align__(16) float pws[];
+  float* As = pws;                 // [C][P]      A[o][i] at [i][o]
+  float* Zs = As + C * P;          // [K2][P]     Zb[s][o][y][k] at [k][o]
+  float* Gs = Zs + K2 * P;         // [K2][kPwNT] G[k][x0 + px]
+  float* Vs = Gs + K2 * kPwNT;     // [C][kPwNT]  in[s][i][y][x0 + px]
+  const int tid = threadIdx.x, x0 = blockIdx.x * kPwNT, y = blockIdx.y, s = blockIdx.z;
+  const long long N = (long long)H * W, row = (long long)y * W + x0;
+  const int nx = min(kPwNT, W - x0);
+  for (int e = tid; e < C * C; e += NT) cp_async_4(&As[(e % C) * P + e / C], &A[e]);
+  const float* zrow = Zb + ((long long)s * C * H + y) * K2;   // + o H K2 + k
+  for (int e = tid; e < K2 * C; e += NT) {
+    const int o = e / K2, k = e % K2;
+    cp_async_4(&Zs[k * P + o], &zrow[(long long)o * H * K2 + k]);
+  }
+  const float* vin = in + (long long)s * C * N + row;
+  const bool vec = (W & 3) == 0;   // (then nx is a multiple of 4 too)
+  if (vec) {
+    constexpr int Q = kPwNT / 4;
+    for (int e = tid; e < K2 * Q; e += NT) {
+      const int k = e / Q, px = 4 * (e % Q);
+      if (px < nx) cp_async_16(&Gs[k * kPwNT + px], &G[(long long)k * W + x0 + px]);
+    }
+    for (int e = tid; e < C * Q; e += NT) {
+      const int i = e / Q, px = 4 * (e % Q);
+      if (px < nx) cp_async_16(&Vs[i * kPwNT + px], &vin[(long long)i * N + px]);
+    }
+  } else {
+    for (int e = tid; e < K2 * kPwNT; e += NT) {
+      const int k = e / kPwNT, px = e % kPwNT;
+      if (px < nx) cp_async_4(&Gs[e], &G[(long long)k * W + x0 + px]);
+    }
+    for (int e = tid; e < C * kPwNT; e += NT) {
+      const int i = e / kPwNT, px = e % kPwNT;
+      if (px < nx) cp_async_4(&Vs[e], &vin[(long long)i * N + px]);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int g = tid / (kPwNT / 4), q = tid % (kPwNT / 4);
+  if (4 * q >= nx) return;
+  float acc[8][4];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const float b = __ldg(&bias[8 * g + o]);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[o][p] = b;
+  }
+#pragma unroll 2
+  for (int k = 0; k < K2; ++k) {
+    const float4 gv = *reinterpret_cast<const float4*>(&Gs[k * kPwNT + 4 * q]);
+    const float4 z0 = *reinterpret_cast<const float4*>(&Zs[k * P + 8 * g]);
+    const float4 z1 = *reinterpret_cast<const float4*>(&Zs[k * P + 8 * g + 4]);
+    const float zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w}, gg[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) acc[o][p] = fmaf(zz[o], gg[p], acc[o][p]);
+  }
+#pragma unroll 4
+  for (int i = 0; i < C; ++i) {
+    const float4 vv = *reinterpret_cast<const float4*>(&Vs[i * kPwNT + 4 * q]);
+    const float4 a0 = *reinterpret_cast<const float4*>(&As[i * P + 8 * g]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&As[i * P + 8 * g + 4]);
+    const float aa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, vq[4] = {vv.x, vv.y, vv.z, vv.w};
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) acc[o][p] = fmaf(aa[o], vq[p], acc[o][p]);
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const long long ob = ((long long)s * C + 8 * g + o) * N + row + 4 * q;
+    if (vec) {
+      *reinterpret_cast<float4*>(out + ob) = make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+      if (ACT == 1)
+        *reinterpret_cast<float4*>(act + ob) =
+            make_float4(gelu_f(acc[o][0]), gelu_f(acc[o][1]), gelu_f(acc[o][2]), gelu_f(acc[o][3]));
+      if (ACT == 2) *reinterpret_cast<float4*>(act + ob) = make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+      continue;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (4 * q + p >= nx) break;
+      out[ob + p] = acc[o][p];
+      if (ACT == 1) act[ob + p] = gelu_f(acc[o][p]);
+      if (ACT == 2) act[ob + p] = acc[o][p];
+    }
+  }
+}
+
+size_t layer_pw_smem(int C, int K2) {
+  return ((size_t)(C + K2) * pw_pitch(C) + (size_t)(K2 + C) * kPwNT) * sizeof(float);
+}
+
+// (the shared-memory limit is raised by layer_pw_prepare, outside any graph capture)
+template <int C, int ACT>
+void launch_layer_pw(cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias, const float* in,
+                     const float* Zb, const float* G, float* out, float* act) {
+  const dim3 grid((W + kPwNT - 1) / kPwNT, H, S);
+  k_layer_pw<C, ACT><<<grid, C * 4, layer_pw_smem(C, K2), s>>>(H, W, K2, A, bias, in, Zb, G, out, act);
+}
+
+template <int C>
+bool layer_pw_attr(size_t smem) {
+  return smem <= 48 * 1024 ||
+         (cudaFuncSetAttribute(k_layer_pw<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+              cudaSuccess &&
+          cudaFuncSetAttribute(k_layer_pw<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+              cudaSuccess);
+}
+
+// whether the register-blocked layer kernel serves this width and mode count
+// (raises its shared-memory limit where needed; called at creation)
+bool layer_pw_prepare(int C, int K2) {
+  const size_t smem = layer_pw_smem(C, K2);
+  if (smem > 200 * 1024) return false;
+  bool ok = false;
+  switch (C) {
+    case 8: ok = layer_pw_attr<8>(smem); break;
+    case 16: ok = layer_pw_attr<16>(smem); break;
+    case 32: ok = layer_pw_attr<32>(smem); break;
+    default: return false;
+  }
+  if (!ok) (void)cudaGetLastError();   // (a refused limit is not an error of the context)
+  return ok;
+}
+
 template <int CI, int CO, bool SPEC, int ACT>
 void launch_pw(cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias, const float* in,
                const float* Zb, const float* G, float* out, float* act) {
@@ -542,28 +718,35 @@ void launch_pw(cudaStream_t s, int S, int H, int W, int K2, const float* A, cons
 // then takes the GEMM path)
 enum PwKind { kPwLayer, kPwLift, kPwProject };
 template <int C>
-bool pw_c(PwKind kind, cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias,
+void pw_c(PwKind kind, bool layer_pw, cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias,
           const float* in, const float* Zb, const float* G, float* out, float* act, int act_kind) {
   if (kind == kPwLift) launch_pw<3, C, false, 0>(s, S, H, W, 0, A, bias, in, nullptr, nullptr, out, nullptr);
   else if (kind == kPwProject) launch_pw<C, 3, false, 0>(s, S, H, W, 0, A, bias, in, nullptr, nullptr, out, nullptr);
+  else if (layer_pw && C % 8 == 0 && act_kind == 1)
+    launch_layer_pw<(C % 8 == 0 ? C : 8), 1>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
+  else if (layer_pw && C % 8 == 0)
+    launch_layer_pw<(C % 8 == 0 ? C : 8), 2>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
   else if (act_kind == 1) launch_pw<C, C, true, 1>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
   else launch_pw<C, C, true, 2>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
-  return true;
 }
-bool pointwise(PwKind kind, cudaStream_t s, int S, int C, int H, int W, int K2, const float* A, const float* bias,
-               const float* in, const float* Zb, const float* G, float* out, float* act, int act_kind) {
+// layer_pw: layer_pw_prepare(C, K2) succeeded (the register-blocked layer kernel)
+bool pointwise(PwKind kind, bool layer_pw, cudaStream_t s, int S, int C, int H, int W, int K2, const float* A,
+               const float* bias, const float* in, const float* Zb, const float* G, float* out, float* act,
+               int act_kind) {
   if (H > 65535 || S > 65535) return false;
+  if (C != 4 && C != 8 && C != 16 && C != 32) return false;
   const int ci = kind == kPwLift ? 3 : C, co = kind == kPwProject ? 3 : C;
-  if (((long long)(ci + (kind == kPwLayer ? K2 : 0)) * pw_pitch(co) + (kind == kPwLayer ? (long long)K2 * kPwNT : 0)) *
-          4 > 49152)
+  if (!(kind == kPwLayer && layer_pw) &&
+      ((long long)(ci + (kind == kPwLayer ? K2 : 0)) * pw_pitch(co) + (kind == kPwLayer ? (long long)K2 * kPwNT : 0)) *
+              4 > 49152)
     return false;
   switch (C) {
-    case 4: return pw_c<4>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
-    case 8: return pw_c<8>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
-    case 16: return pw_c<16>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
-    case 32: return pw_c<32>(kind, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind);
-    default: return false;
+    case 4: pw_c<4>(kind, layer_pw, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind); break;
+    case 8: pw_c<8>(kind, layer_pw, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind); break;
+    case 16: pw_c<16>(kind, layer_pw, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind); break;
+    default: pw_c<32>(kind, layer_pw, s, S, H, W, K2, A, bias, in, Zb, G, out, act, act_kind); break;
   }
+  return true;
 }
 
 // O[s][o][m] = sum_i R[o][i][m] V[s][i][m]   (conj: sum_o conj(R[o][i][m]) V[s][o][m] -> O[s][i][m])
@@ -709,6 +892,7 @@ struct mm_fno {
   bool own_stream = false;
   int C = 0, L = 0, Mx = 0, My = 0, H = 0, W = 0, J = 0, Smax = 0;
   int sms = 1;                  // multiprocessors of the device
+  bool layer_pw = false;        // the register-blocked layer kernel serves (C, 2 Mx)
   long long N = 0, nparam = 0;
   long long xslice = 0;         // floats between the split-K slices of X and Z
   std::vector<long long> off;   // P, p, {W, b, R} per layer, Q, q
@@ -771,7 +955,7 @@ void fwd(mm_fno* f, int S) {
   const YTile yt = ytile(S, C, H, J, Mx, f->sms);
   const int xp = xparts(f, S, yt);
   // lift: v0[C x N] = P[C x 3] u[3 x N] + p
-  if (!pointwise(kPwLift, s, S, C, H, W, 0, P_(f, 0), P_(f, 1), f->u, nullptr, nullptr, f->v[0], nullptr, 0))
+  if (!pointwise(kPwLift, f->layer_pw, s, S, C, H, W, 0, P_(f, 0), P_(f, 1), f->u, nullptr, nullptr, f->v[0], nullptr, 0))
     gemm(s, false, false, S, gargs(C, (int)N, 3, P_(f, 0), 3, 0, f->u, N, 3 * N, f->v[0], N, CN, 1.f, 0.f, P_(f, 1)));
   for (int l = 0; l < L; ++l) {
     float* vin = f->v[l];
@@ -784,7 +968,7 @@ void fwd(mm_fno* f, int S) {
     yexpand(s, yt, S, C, H, J, Mx, f->O, f->Gy, false, f->Z);
     // z = Z_blk [C H x 2Mx] . Gblk [2Mx x W] (spectral part) + W v + b, and
     // v_{l+1} = GELU(z) (z after the last layer)
-    if (!pointwise(kPwLayer, s, S, C, H, W, 2 * Mx, P_(f, sW(l)), P_(f, sb(l)), vin, f->Z, f->Gblk, f->z[l],
+    if (!pointwise(kPwLayer, f->layer_pw, s, S, C, H, W, 2 * Mx, P_(f, sW(l)), P_(f, sb(l)), vin, f->Z, f->Gblk, f->z[l],
                    f->v[l + 1], l < L - 1 ? 1 : 2)) {
       gemm(s, false, false, S, gargs(C * H, W, 2 * Mx, f->Z, 2 * Mx, (long long)C * H * 2 * Mx, f->Gblk, W, 0,
                                      f->z[l], W, CN));
@@ -793,7 +977,7 @@ void fwd(mm_fno* f, int S) {
     }
   }
   // project: y[3 x N] = Q[3 x C] v_L + q
-  if (!pointwise(kPwProject, s, S, C, H, W, 0, P_(f, q), P_(f, qq), f->v[L], nullptr, nullptr, f->yh, nullptr, 0))
+  if (!pointwise(kPwProject, f->layer_pw, s, S, C, H, W, 0, P_(f, q), P_(f, qq), f->v[L], nullptr, nullptr, f->yh, nullptr, 0))
     gemm(s, false, false, S, gargs(3, (int)N, C, P_(f, q), C, 0, f->v[L], N, CN, f->yh, N, 3 * N, 1.f, 0.f, P_(f, qq)));
 }
 
@@ -861,6 +1045,7 @@ int mm_fno_create(mm_fno** out, int H, int W, const mm_fno_cfg* cfg, int device,
   mm_fno* f = new mm_fno();
   f->device = device;
   f->sms = sms;
+  f->layer_pw = layer_pw_prepare(C, 2 * Mx);
   f->C = C; f->L = L; f->Mx = Mx; f->My = My; f->H = H; f->W = W; f->J = 2 * My; f->Smax = Smax;
   f->N = (long long)H * W;
   auto cleanup = [&](int code) { mm_fno_destroy(f); return code; };

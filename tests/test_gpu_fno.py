@@ -47,11 +47,12 @@ def cosine(a, b):
 # tiled y product with ragged row stages, several GEMM tiles and split-K
 # slices of the x products (96 x 128, Mx = 40); more x modes than one block
 # has threads (Mx = 260: the untiled y product, and tables too large for the
-# fused layer kernel); rows of 200 pixels (a ragged block of the pointwise
-# kernels); a width without a pointwise instantiation (C = 6: the GEMM path
-# for lift, layers and projection)
+# fused layer kernel); rows of 200 pixels (a ragged block of the
+# register-blocked layer kernel, 16-byte copies) and of 130 pixels (4-byte
+# copies: rows not a multiple of 4); a width without a pointwise
+# instantiation (C = 6: the GEMM path for lift, layers and projection)
 FNO_CASES = [(1, 4, 2, 8, 8, 3, 3), (2, 4, 2, 8, 8, 3, 3), (2, 8, 2, 96, 128, 40, 6), (1, 4, 1, 8, 520, 260, 2),
-             (1, 4, 2, 8, 200, 20, 2), (2, 6, 2, 16, 24, 5, 3)]
+             (2, 8, 2, 8, 200, 20, 2), (1, 8, 1, 4, 130, 10, 2), (2, 6, 2, 16, 24, 5, 3)]
 
 
 @pytest.mark.parametrize("S,C,L,H,W,Mx,My", FNO_CASES)
