@@ -36,6 +36,21 @@ __device__ __forceinline__ float gelu_df(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
 }
 
+// 4-, 8- and 16-byte asynchronous global -> shared copies (complete at
+// cp.async.wait_all; both addresses aligned to the copy size)
+__device__ __forceinline__ void cp_async_4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // bfloat16 tensor-core GEMM: C[b] = alpha op(A[b]) op(B[b]) + beta C[b]
 // (+ bias[m]).  op(A)(m, k) = TA ? A[k lda + m] : A[m lda + k];
@@ -385,7 +400,7 @@ __global__ void k_sum_parts(long long n, int parts, long long stride, const floa
 }
 
 // as k_yexpand; block (row group, sc): O[sc] (J x Mx) and F[:, y0 .. y0+YB)
-// staged, YB x Mx outputs
+// staged by asynchronous copies (conj_f applied at use), YB x Mx outputs
 __global__ void __launch_bounds__(kYNT) k_yexpand_t(int H, int J, int Mx, int YB, const float2* __restrict__ O,
                                                   const float2* __restrict__ F, bool conj_f, float* __restrict__ Z) {
   extern __shared__ float2 ysh[];
@@ -394,19 +409,21 @@ __global__ void __launch_bounds__(kYNT) k_yexpand_t(int H, int J, int Mx, int YB
   const long long sc = blockIdx.y;
   const int y0 = blockIdx.x * YB, yn = min(YB, H - y0);
   const int tid = threadIdx.x;
-  for (int e = tid; e < J * Mx; e += kYNT) os[e] = O[sc * J * Mx + e];
+  for (int e = tid; e < J * Mx; e += kYNT) cp_async_8(&os[e], &O[sc * J * Mx + e]);
   for (int e = tid; e < J * yn; e += kYNT) {
     const int j = e / yn, yy = e % yn;
-    float2 f = F[(long long)j * H + y0 + yy];
-    if (conj_f) f.y = -f.y;
-    fs[j * YB + yy] = f;
+    cp_async_8(&fs[j * YB + yy], &F[(long long)j * H + y0 + yy]);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
+  const float cs = conj_f ? -1.f : 1.f;
   for (int e = tid; e < yn * Mx; e += kYNT) {
     const int yy = e / Mx, k = e % Mx;
     float re = 0.f, im = 0.f;
     for (int j = 0; j < J; ++j) {
-      const float2 f = fs[j * YB + yy], o = os[j * Mx + k];
+      float2 f = fs[j * YB + yy];
+      f.y *= cs;
+      const float2 o = os[j * Mx + k];
       re = fmaf(f.x, o.x, fmaf(-f.y, o.y, re));
       im = fmaf(f.x, o.y, fmaf(f.y, o.x, im));
     }
@@ -485,16 +502,6 @@ void yexpand(cudaStream_t s, const YTile& t, int S, int C, int H, int J, int Mx,
 constexpr int kPwNT = 128;
 __host__ __device__ constexpr int pw_pitch(int co) { return (co + 3) / 4 * 4 + 4; }
 
-// 4- and 16-byte asynchronous global -> shared copies (complete at
-// cp.async.wait_all; the 16-byte form needs both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async_4(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_16(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
 
 template <int CI, int CO, bool SPEC, int ACT>
 __global__ void __launch_bounds__(kPwNT) k_pointwise(int H, int W, int K2, const float* __restrict__ A,
@@ -750,24 +757,37 @@ bool pointwise(PwKind kind, bool layer_pw, cudaStream_t s, int S, int C, int H, 
 }
 
 // O[s][o][m] = sum_i R[o][i][m] V[s][i][m]   (conj: sum_o conj(R[o][i][m]) V[s][o][m] -> O[s][i][m])
+// Four lanes per output (kMixLanes consecutive threads), each summing
+// i = part, part + 4, ..., then a fixed two-step shuffle sum.  Launch with
+// kMixLanes * S * C * NM threads in blocks of a multiple of 32.
+constexpr int kMixLanes = 4;
 __global__ void k_mix(int S, int C, int NM, const float2* __restrict__ R, const float2* __restrict__ V,
                       float2* __restrict__ O, bool adjoint) {
   const long long total = (long long)S * C * NM;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int m = (int)(idx % NM), o = (int)((idx / NM) % C);
-  const long long s = idx / ((long long)NM * C);
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = gt / kMixLanes;
+  const int part = (int)(gt % kMixLanes);
+  const bool on = idx < total;   // (every lane stays for the shuffles)
   float re = 0.f, im = 0.f;
-#pragma unroll 8
-  for (int i = 0; i < C; ++i) {
-    float2 r = adjoint ? R[((long long)i * C + o) * NM + m] : R[((long long)o * C + i) * NM + m];
-    if (adjoint) r.y = -r.y;
-    const float2 v = V[(s * C + i) * NM + m];
-    re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
-    im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
+  if (on) {
+    const int m = (int)(idx % NM), o = (int)((idx / NM) % C);
+    const long long s = idx / ((long long)NM * C);
+#pragma unroll 4
+    for (int i = part; i < C; i += kMixLanes) {
+      float2 r = adjoint ? R[((long long)i * C + o) * NM + m] : R[((long long)o * C + i) * NM + m];
+      if (adjoint) r.y = -r.y;
+      const float2 v = V[(s * C + i) * NM + m];
+      re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
+      im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
+    }
   }
-  O[idx] = make_float2(re, im);
+  re += __shfl_xor_sync(0xffffffffu, re, 1);
+  im += __shfl_xor_sync(0xffffffffu, im, 1);
+  re += __shfl_xor_sync(0xffffffffu, re, 2);
+  im += __shfl_xor_sync(0xffffffffu, im, 2);
+  if (on && part == 0) O[idx] = make_float2(re, im);
 }
+unsigned mix_blocks(long long outputs) { return (unsigned)((outputs * kMixLanes + 255) / 256); }
 
 // dR[o][i][m] += sum_s dO[s][o][m] conj(V[s][i][m])
 __global__ void k_dR(int S, int C, int NM, const float2* __restrict__ dO, const float2* __restrict__ V,
@@ -963,7 +983,7 @@ void fwd(mm_fno* f, int S) {
     gemm(s, false, false, S, sliced(gargs(C * H, 2 * Mx, W, vin, W, CN, f->Fblk, 2 * Mx, 0, f->X, 2 * Mx,
                                           (long long)C * H * 2 * Mx), xp, f->xslice));
     ysum(s, yt, S, C, H, J, Mx, f->X, true, xp, f->xslice, f->Fy, false, f->V[l], f->Yp);
-    k_mix<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
+    k_mix<<<mix_blocks((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
                                                       f->V[l], f->O, false);
     yexpand(s, yt, S, C, H, J, Mx, f->O, f->Gy, false, f->Z);
     // z = Z_blk [C H x 2Mx] . Gblk [2Mx x W] (spectral part) + W v + b, and
@@ -1014,7 +1034,7 @@ void bwd(mm_fno* f, int S, const float* y) {
     ysum(s, yt, S, C, H, J, Mx, f->Z, true, xp, f->xslice, f->Gy, true, f->dO, f->Yp);
     k_dR<<<nb((long long)C * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, f->dO, f->V[l],
                                                       reinterpret_cast<float2*>(G_(f, sR(l))));
-    k_mix<<<nb((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
+    k_mix<<<mix_blocks((long long)S * C * J * Mx), 256, 0, s>>>(S, C, J * Mx, reinterpret_cast<const float2*>(P_(f, sR(l))),
                                                       f->dO, f->dV, true);
     yexpand(s, yt, S, C, H, J, Mx, f->dV, f->Fy, true, f->X);
     // dv2 += dX_blk [C H x 2Mx] . Fblk^T [2Mx x W]

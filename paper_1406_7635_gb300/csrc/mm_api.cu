@@ -692,7 +692,7 @@ int mm_set_fixed_dt_sequence(mm_ctx* c, const double* dts, int n) {
   return write_state(c);
 }
 
-// Exact-path judge of the surrogate: relative L2 difference of the two
+// Exact-path check of the surrogate: relative L2 difference of the two
 // demag fields at the current m; above the tolerance the context falls back
 // to the exact convolution for the rest of its life.
 static int surrogate_check(mm_ctx* c) {
