@@ -686,20 +686,24 @@ void launch_layer_pw(cudaStream_t s, int S, int H, int W, int K2, const float* A
   k_layer_pw<C, ACT><<<grid, C * 4, layer_pw_smem(C, K2), s>>>(H, W, K2, A, bias, in, Zb, G, out, act);
 }
 
+// The limit is raised to the fixed cap, not to one network's need, so that a
+// later network of the same width never lowers it below an earlier one's.
+constexpr int kLayerPwSmemCap = 200 * 1024;
 template <int C>
 bool layer_pw_attr(size_t smem) {
   return smem <= 48 * 1024 ||
-         (cudaFuncSetAttribute(k_layer_pw<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+         (cudaFuncSetAttribute(k_layer_pw<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLayerPwSmemCap) ==
               cudaSuccess &&
-          cudaFuncSetAttribute(k_layer_pw<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+          cudaFuncSetAttribute(k_layer_pw<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLayerPwSmemCap) ==
               cudaSuccess);
 }
 
 // whether the register-blocked layer kernel serves this width and mode count
-// (raises its shared-memory limit where needed; called at creation)
+// (raises its shared-memory limit where needed; called at creation, outside
+// any graph capture)
 bool layer_pw_prepare(int C, int K2) {
   const size_t smem = layer_pw_smem(C, K2);
-  if (smem > 200 * 1024) return false;
+  if (smem > (size_t)kLayerPwSmemCap) return false;
   bool ok = false;
   switch (C) {
     case 8: ok = layer_pw_attr<8>(smem); break;

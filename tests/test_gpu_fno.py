@@ -136,3 +136,25 @@ def test_guard_falls_back_to_exact_path(mm):
     ctx.close()
     ctx2.close()
     net.close()
+
+
+def test_two_networks_of_one_width_coexist(mm):
+    """A second network of the same width whose layer kernel needs less shared
+    memory (both above the 48 KB default) leaves the first one working and
+    unchanged: the kernels' limit is raised to a fixed cap, never lowered."""
+    H, W = 8, 128
+    a = mm.FNO(H, W, width=8, layers=1, modes_x=48, modes_y=2, max_batch=1, seed=1)   # 58 KB of tables
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    u = torch.randn(3 * H * W, device="cuda", generator=g)
+    y1 = torch.empty_like(u)
+    a.forward(u, y1, 1)
+    b = mm.FNO(H, W, width=8, layers=1, modes_x=40, modes_y=2, max_batch=1, seed=2)   # 49 KB of tables
+    y2 = torch.empty_like(u)
+    a.forward(u, y2, 1)
+    yb = torch.empty_like(u)
+    b.forward(u, yb, 1)
+    assert torch.equal(y1, y2)   # (the forward pass is deterministic)
+    assert bool(torch.isfinite(yb).all())
+    a.close()
+    b.close()
