@@ -1,6 +1,7 @@
 """Pins for the float64 FNO oracle: the truncated spectral operator reproduces
-band-limited inputs exactly, and every analytic gradient matches central
-finite differences of the oracle's own loss."""
+band-limited inputs exactly and equals numpy's FFT truncation on any input,
+GELU matches the tabulated normal distribution, and every analytic gradient
+matches central finite differences of the oracle's own loss."""
 import numpy as np
 import pytest
 
@@ -59,3 +60,39 @@ def test_gradients_match_finite_differences(tiny):
                 fd = (lp - lm) / (2 * h)
                 an = g[name][idx].real if part == 1.0 else g[name][idx].imag
                 assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-9, (name, idx, part, fd, an)
+
+
+def test_spectral_operator_is_the_fft_truncation():
+    """With R = identity per mode, K v of any real input equals numpy's 2-D
+    FFT with every mode outside {kx < Mx} x {ky < My or ky >= H - My} zeroed,
+    the kept kx > 0 columns doubled (they stand for their conjugate
+    partners), inverted and the real part taken."""
+    H, W, Mx, My, C = 12, 10, 4, 3, 3
+    mats = dft_mats(H, W, Mx, My)
+    R = np.zeros((C, C, 2 * My, Mx), dtype=complex)
+    for i in range(C):
+        R[i, i] = 1.0
+    v = np.random.default_rng(5).standard_normal((C, H, W))
+    out, V = spectral(v, R, mats)
+    mask = np.zeros((H, W))
+    rows = list(range(My)) + list(range(H - My, H))
+    for ky in rows:
+        mask[ky, 0] = 1.0
+        mask[ky, 1:Mx] = 2.0
+    ref = np.real(np.fft.ifft2(np.fft.fft2(v) * mask[None]))
+    assert np.abs(out - ref).max() < 1e-12
+    # the cached coefficients are the FFT's at the kept modes
+    assert np.abs(V - np.fft.fft2(v)[:, rows, :Mx]).max() < 1e-10
+
+
+def test_gelu_against_the_normal_distribution():
+    """GELU(x) = x Phi(x) with tabulated Phi(1) = 0.8413447460685429 and
+    Phi(3) = 0.9986501019683699; its derivative matches central differences."""
+    from oracle.fno import gelu, gelu_grad
+    x = np.array([1.0, -1.0, 0.0, 3.0])
+    want = np.array([0.8413447460685429, -(1 - 0.8413447460685429), 0.0, 3 * 0.9986501019683699])
+    assert np.abs(gelu(x) - want).max() < 1e-15
+    xs = np.linspace(-4, 4, 33)
+    h = 1e-6
+    fd = (gelu(xs + h) - gelu(xs - h)) / (2 * h)
+    assert np.abs(gelu_grad(xs) - fd).max() < 1e-8
