@@ -262,10 +262,14 @@ int mm_sync(mm_ctx* ctx);
  *   v_0 = P u + p;  v_{l+1} = act(W_l v_l + b_l + K_l v_l);  y = Q v_L + q,
  * act = GELU (none after the last layer), K_l the spectral convolution
  * truncated to kx < modes_x and ky in {0..modes_y-1} U {H-modes_y..H-1},
- * written with explicit partial DFTs (Re of the inverse).  Dense products run
- * on the bfloat16 tensor cores with float32 accumulation; parameters are
- * float32 (Adam), flat in the order P, p, {W_l, b_l, R_l}, Q, q with R_l
- * complex [width][width][2 modes_y][modes_x] as (re, im) pairs.
+ * written with explicit partial DFTs (Re of the inverse).  The x-direction
+ * partial DFTs and the gradient products run on the bfloat16 tensor cores
+ * with float32 accumulation; for widths 4, 8, 16 and 32 the forward pass's
+ * pointwise products (lift, W_l v + b_l with the inverse x partial DFT and
+ * the GELU, projection) run in float32, fused per layer.  The forward pass
+ * is deterministic (fixed summation orders).  Parameters are float32 (Adam),
+ * flat in the order P, p, {W_l, b_l, R_l}, Q, q with R_l complex
+ * [width][width][2 modes_y][modes_x] as (re, im) pairs.
  * Loss: sum |yhat - y|^2 / sum |y|^2 over a batch. */
 typedef struct mm_fno mm_fno;
 typedef struct {
@@ -273,12 +277,17 @@ typedef struct {
   int max_batch;               /* samples per forward/backward call        */
   unsigned long long seed;     /* initial parameters                       */
 } mm_fno_cfg;
+/* ny = H, nx = W.  MM_ERR_ARG unless H, W >= 2, width, layers, max_batch >= 1,
+ * modes_x <= W / 2 and 2 modes_y <= H (checked before any device call);
+ * MM_ERR_OOM / MM_ERR_CUDA from the allocations.  cuda_stream NULL: the
+ * network creates its own stream. */
 int mm_fno_create(mm_fno** out, int ny, int nx, const mm_fno_cfg* cfg, int device, void* cuda_stream);
 int mm_fno_destroy(mm_fno* f);
 long long mm_fno_param_count(mm_fno* f);
 int mm_fno_get_params(mm_fno* f, float* host, long long n);
 int mm_fno_set_params(mm_fno* f, const float* host, long long n);   /* resets Adam */
-/* Device pointers, float32 [S][3][ny][nx]. */
+/* Device pointers, float32 [S][3][ny][nx], 1 <= S <= max_batch (else
+ * MM_ERR_ARG); returns after the network's stream is idle. */
 int mm_fno_forward(mm_fno* f, const float* u, float* y, int S);
 /* Loss and its gradient (host array of param_count floats, may be NULL). */
 int mm_fno_grad(mm_fno* f, const float* u, const float* y, int S, float* grad_host, double* loss);
