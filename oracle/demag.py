@@ -19,6 +19,9 @@ the axis), i.e. every offset of the 2 P N - 1 cells centred on the target;
 this reading reproduces the film column of Table tabPBC1 within its printed
 accuracy.  The convolution along a periodic axis is then cyclic with period
 N (no padding), with the tensor summed over the offsets D = d mod N.
+
+Float64 test infrastructure only: tests, smoke() and the benchmark's CPU
+legs use it; the product path never does.
 """
 import numpy as np
 

@@ -6,6 +6,9 @@ E_anis  = -1/2 sum M.B_anis(Ku1) V - 1/4 sum M.B_anis(Ku2) V   (Eq. EaniUM)
 E_Z     = -sum M.B_ext V                 (Zeeman energy density -M.B)
 E_DM    = -1/2 sum M.B_DM V              (Eq. eqEdensDMI)
 <m>     = average of m over the magnetic cells.
+
+Float64 test infrastructure only: tests, smoke() and the benchmark's CPU
+legs use it; the product path never does.
 """
 import numpy as np
 

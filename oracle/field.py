@@ -4,6 +4,9 @@ B_eff = B_ext + B_demag + B_exch + B_anis + B_DM (the interfacial DMI term
 and its boundary conditions are in dmi.py; thermal and spin-transfer terms
 are outside this path).  Non-magnetic cells (mask 0 or Msat 0) carry m = 0,
 B_eff = 0 and zero torque.
+
+Float64 test infrastructure only: tests, smoke() and the benchmark's CPU
+legs use it; the product path never does.
 """
 import numpy as np
 

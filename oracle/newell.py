@@ -17,6 +17,9 @@ here the same definite integral is evaluated two ways:
 Convention (reading of the sign used by the tables of Sec. III.B, which print
 N = H/M < 0): N is stored positive, so that the self term of a cube is +1/3,
 the trace of every self term is 1, and B_demag = -mu0 * N * M.
+
+Float64 test infrastructure only: tests, smoke() and the benchmark's CPU
+legs use it; the product path never does.
 """
 import numpy as np
 

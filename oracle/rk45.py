@@ -15,6 +15,9 @@ Readings where the paper is silent:
   as the next k1; only then is m normalised per cell (m has unit length);
 * run(t_end) shortens the last step to land on t_end exactly; the step size the
   controller proposes after it is kept for the next call.
+
+Float64 test infrastructure only: tests, smoke() and the benchmark's CPU
+legs use it; the product path never does.
 """
 from fractions import Fraction as F
 
