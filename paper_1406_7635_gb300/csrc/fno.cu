@@ -723,11 +723,12 @@ void launch_pw(cudaStream_t s, int S, int H, int W, int K2, const float* A, cons
   k_pointwise<CI, CO, SPEC, ACT><<<grid, kPwNT, smem, s>>>(H, W, K2, A, bias, in, Zb, G, out, act);
 }
 
-// the layer output (CI = CO = C, spectral part, act 1 GELU / 2 copy), the lift
-// (CI = 3) and the projection (CO = 3) for C in {4, 8, 16, 32}; false where
-// there is no instantiation or the staged tables exceed 48 KB (the caller
-// then takes the GEMM path)
+// The pointwise passes: the layer output (CI = CO = C, spectral part, act 1
+// GELU / 2 copy), the lift (CI = 3) and the projection (CO = 3).
 enum PwKind { kPwLayer, kPwLift, kPwProject };
+// (the register-blocked layer kernel exists for C a multiple of 8; its
+// template argument is clamped so that the untaken branch still compiles
+// for C = 4)
 template <int C>
 void pw_c(PwKind kind, bool layer_pw, cudaStream_t s, int S, int H, int W, int K2, const float* A, const float* bias,
           const float* in, const float* Zb, const float* G, float* out, float* act, int act_kind) {
@@ -740,7 +741,10 @@ void pw_c(PwKind kind, bool layer_pw, cudaStream_t s, int S, int H, int W, int K
   else if (act_kind == 1) launch_pw<C, C, true, 1>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
   else launch_pw<C, C, true, 2>(s, S, H, W, K2, A, bias, in, Zb, G, out, act);
 }
-// layer_pw: layer_pw_prepare(C, K2) succeeded (the register-blocked layer kernel)
+// Launches one pointwise pass for C in {4, 8, 16, 32}; false where there is
+// no instantiation or the staged tables exceed 48 KB (the caller then takes
+// the GEMM path).  layer_pw: layer_pw_prepare(C, K2) succeeded (the
+// register-blocked layer kernel serves the layer output).
 bool pointwise(PwKind kind, bool layer_pw, cudaStream_t s, int S, int C, int H, int W, int K2, const float* A,
                const float* bias, const float* in, const float* Zb, const float* G, float* out, float* act,
                int act_kind) {
