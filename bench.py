@@ -8,17 +8,23 @@ error reduction and step control) over the whole grid.
 Default workload: the 3-D ellipsoid, 128 x 128 x 32 cells of 3 nm (demag
 convolution padded to 256 x 256 x 64), the configuration on which both the
 cell-steps/s and the HBM-roofline fraction of the demag convolution are
-quoted; the 256 x 256 x 1 grain film is reported beside it ("film").
+quoted; the 256 x 256 x 1 grain film is reported beside it ("film"), and the
+contexts that step with the general kernels (spin-transfer torques, a
+periodic x axis) beside that ("general_path").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Multi-GPU: the path does not shard (one simulation per GPU); N ranks run N
 independent replicas ("replicas only", weak scaling), no collective on the
 data path.
+
+The reference arm (--impl reference) is the float64 oracle: one replica per
+host core, each stepping the same workload, on rank 0 only.
 """
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -63,6 +69,24 @@ def measured_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def host_description():
+    """Core count and CPU model of this host."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return {"nproc": cores, "cpu_model": model, "machine": platform.machine()}
 
 
 class ClockSampler:
@@ -119,39 +143,65 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------------
+# Algorithmic bytes and flops of the demag convolution (per evaluation)
+# ---------------------------------------------------------------------------
 def _pad(n):
     return 1 if n == 1 else 1 << (2 * n - 2).bit_length()
 
 
-def algorithmic_demag_bytes(p):
-    """Minimum HBM bytes of one demag convolution (50 B per cell at 128 x 128
-    x 32): read m (3 x 4 B) and the mask/region bytes (2 B) per cell, the
-    kernel spectrum octant (6 float32 per octant point), write B (3 x 4 B)
-    per cell."""
+def _spectrum_rows_bytes(p):
+    """Complex float32 bytes of the x-transformed spectrum rows that carry
+    data: 3 components x (px/2 + 1) x ny x nz (12.68 MB at 128 x 128 x 32)."""
+    px = _pad(p.nx)
+    hx = px // 2 + 1 if px > 1 else 1
+    return 3 * 8 * hx * p.ny * p.nz
+
+
+def _octant_bytes(p):
+    """The float32 kernel spectrum octant: 6 components (13.18 MB at 128 x
+    128 x 32)."""
     def half(n):
         return 1 if n == 1 else _pad(n) // 2 + 1
-    octant = half(p.nx) * half(p.ny) * half(p.nz)
-    return p.ncells * (12 + 2 + 12) + 6 * 4 * octant
+    return 6 * 4 * half(p.nx) * half(p.ny) * half(p.nz)
+
+
+def algorithmic_demag_bytes(p):
+    """Minimum HBM bytes of one demag convolution (51 B per cell at 128 x 128
+    x 32): read m (3 x 4 B) and the mask/region bytes (2 B) per cell, the
+    kernel spectrum octant, write B (3 x 4 B) per cell."""
+    return p.ncells * (12 + 2 + 12) + _octant_bytes(p)
+
+
+def five_pass_passes(p):
+    """HBM bytes of each pass of the unfused five-pass design (x R2C, y,
+    z*K*z^-1, y^-1, x C2R, each pass through memory, pruned to the rows that
+    carry data; 2-D: x, y*K*y^-1, x^-1): at 128 x 128 x 32 20.0 / 38.0 / 63.9 /
+    38.0 / 19.0 MB, 341 B per cell in all."""
+    py, pz = _pad(p.ny), _pad(p.nz)
+    x_out = _spectrum_rows_bytes(p)
+    y_out = x_out // p.ny * py
+    kern = _octant_bytes(p)
+    pass1 = p.ncells * (12 + 2) + x_out
+    last = x_out + 12 * p.ncells
+    if pz == 1:
+        return [pass1, 2 * x_out + kern, last]
+    return [pass1, x_out + y_out, 2 * y_out + kern, y_out + x_out, last]
 
 
 def five_pass_demag_bytes(p):
-    """HBM bytes of the unfused five-pass design (x R2C, y, z*K*z^-1, y^-1,
-    x C2R, each pass through memory, pruned to the rows that carry data):
-    340 B per cell at 128 x 128 x 32."""
-    px, py, pz = _pad(p.nx), _pad(p.ny), _pad(p.nz)
-    hx = px // 2 + 1 if px > 1 else 1
-    c8 = 3 * 8
-    x_out = c8 * hx * p.ny * p.nz
-    y_out = c8 * hx * py * p.nz
-    pass1 = p.ncells * (12 + 2) + x_out
-    kern = algorithmic_demag_bytes(p) - p.ncells * 26
-    if pz == 1:                                   # 2-D: y*K*y^-1 is one pass
-        return pass1 + 2 * x_out + kern + x_out + 12 * p.ncells
-    pass2 = x_out + y_out
-    pass3 = 2 * y_out + kern                      # z pruned both ways, + kernel
-    pass4 = y_out + x_out
-    pass5 = x_out + 12 * p.ncells
-    return pass1 + pass2 + pass3 + pass4 + pass5
+    return sum(five_pass_passes(p))
+
+
+def yz_kernel_bytes(p):
+    """The (y, z) kernel's share of the five-pass bytes: the passes it fuses
+    (y, z*K*z^-1, y^-1; in 2-D y*K*y^-1): 139.98 MB (267 B per cell) at 128 x
+    128 x 32; and its own floor: read the spectrum rows and the octant, write
+    the spectrum rows (38.5 MB)."""
+    passes = five_pass_passes(p)
+    fused = sum(passes[1:-1])
+    floor = 2 * _spectrum_rows_bytes(p) + _octant_bytes(p)
+    return fused, floor
 
 
 def algorithmic_demag_flops(p):
@@ -160,49 +210,155 @@ def algorithmic_demag_flops(p):
     over the lines that carry data (x: ny*nz rows per component, y: hx*nz
     columns, z: hx*py columns), forward and inverse, plus the spectral
     product (30 flops per frequency point in 3-D, 14 in 2-D where Kxz = Kyz
-    = 0).  823 MFLOP at 128 x 128 x 32."""
+    = 0).  823 MFLOP at 128 x 128 x 32, of which the (y, z) kernel's share
+    (y, z and the product) is 695 MFLOP."""
+    return sum(demag_flops_parts(p))
+
+
+def demag_flops_parts(p):
+    """(x transforms, y and z transforms plus the product) flops."""
     from math import log2
     px, py, pz = _pad(p.nx), _pad(p.ny), _pad(p.nz)
     hx = px // 2 + 1 if px > 1 else 1
+    fx = 2 * 3 * p.ny * p.nz * 2.5 * px * log2(px) if px > 1 else 0.0
     f = 0.0
-    if px > 1:
-        f += 2 * 3 * p.ny * p.nz * 2.5 * px * log2(px)
     if py > 1:
         f += 2 * 3 * hx * p.nz * 5 * py * log2(py)
     if pz > 1:
         f += 2 * 3 * hx * py * 5 * pz * log2(pz)
     f += (30 if pz > 1 else 14) * hx * py * pz
-    return f
+    return fx, f
 
 
-# FP32 issue peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x
-# 2.070 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-
-CONV_SOURCES = ("paper_1406_7635_gb300/csrc/fft_fused.cu", "paper_1406_7635_gb300/csrc/fft.cuh")
+YZ_SOURCES = ("paper_1406_7635_gb300/csrc/fft_fused.cu", "paper_1406_7635_gb300/csrc/fft.cuh")
 
 
-def conv_sources_sha():
+def sources_sha(files):
     import hashlib
     h = hashlib.sha256()
-    for f in CONV_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def conv_traffic(workload):
-    """DRAM bytes of one convolution from the committed ncu summary of the
-    same workload, or None when the convolution's sources changed since the
-    counters were taken."""
-    prof = os.path.join(ROOT, "profiles", f"demag_conv_{workload}.json")
+def yz_traffic(workload):
+    """DRAM bytes of one in-step (y, z) kernel launch from the committed ncu
+    summary of the same workload, or None when the kernel's sources changed
+    since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", f"yz_kernel_{workload}.json")
     if not os.path.exists(prof):
         return None
     with open(prof) as f:
         d = json.load(f)
-    if d.get("src_sha256_16") != conv_sources_sha():
+    if d.get("src_sha256_16") != sources_sha(YZ_SOURCES):
         return None
-    return d.get("dram_bytes_per_conv")
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (float64 numpy): the cpu_baseline legs and the reference arm
+# ---------------------------------------------------------------------------
+def _oracle_worker(name, steps, warmup, budget_s, barrier, queue):
+    """One oracle replica (a spawned process, one thread): kernel set-up and
+    the first stage untimed, `warmup` untimed steps, then wait for the other
+    replicas and time up to `steps` accepted RK45 steps (at least one) within
+    budget_s."""
+    try:
+        from oracle.rk45 import RK45
+        p = WORKLOADS[name]()
+        s = RK45(p)
+        s.k1 = s.field.torque(s.m, 0.0)
+        for _ in range(warmup):
+            s.adaptive_step()
+        if barrier is not None:
+            barrier.wait(timeout=3600)
+        t0 = time.perf_counter()
+        done = 0
+        while done < steps:
+            s.adaptive_step()
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        queue.put((done, time.perf_counter() - t0, p.ncells))
+    except Exception as e:   # reported, never hangs the parent
+        queue.put(("error", repr(e), 0))
+
+
+class single_threaded_children:
+    """While active, processes spawned from here run their numeric libraries
+    on one thread each (the variables are inherited at spawn time)."""
+    KEYS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __enter__(self):
+        self.keep = {k: os.environ.get(k) for k in self.KEYS}
+        for k in self.KEYS:
+            os.environ[k] = "1"
+        return self
+
+    def __exit__(self, *exc):
+        for k, v in self.keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def oracle_replicas(name, replicas, steps, warmup=0, budget_s=60.0):
+    """`replicas` independent oracle processes (spawned, one thread each) on
+    the same workload, timed together after a barrier.  Returns
+    (aggregate cell-steps/s, per-replica steps, slowest replica's seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with single_threaded_children():
+        q = ctx.Queue()
+        bar = ctx.Barrier(replicas) if replicas > 1 else None
+        procs = [ctx.Process(target=_oracle_worker, args=(name, steps, warmup, budget_s, bar, q), daemon=True)
+                 for _ in range(replicas)]
+        for pr in procs:
+            pr.start()
+        res = [q.get(timeout=3600) for _ in procs]
+        for pr in procs:
+            pr.join(timeout=60)
+    bad = [r for r in res if r[0] == "error"]
+    if bad:
+        raise RuntimeError(f"oracle replica failed: {bad[0][1]}")
+    seconds = max(r[1] for r in res)
+    cell_steps = sum(r[0] * r[2] for r in res)
+    return cell_steps / seconds, [r[0] for r in res], seconds
+
+
+def cpu_baseline(name, steps, cores_all):
+    """The oracle on this host: one replica (one core) and one replica per
+    core (all cores, aggregate)."""
+    v1, st1, s1 = oracle_replicas(name, 1, steps)
+    vn, stn, sn = oracle_replicas(name, cores_all, steps)
+    host = host_description()
+    return {"value": vn, "unit": "cell-steps/s", "cores": cores_all, "kind": "oracle",
+            "sample": f"{cores_all} independent float64 numpy oracle replicas (one thread each), "
+                      f"{min(stn)}-{max(stn)} accepted RK45 steps each of the full {name} grid after untimed "
+                      f"kernel set-up, timed together ({sn:.1f} s)",
+            "one_core": {"value": v1, "cores": 1, "steps": st1[0], "seconds": s1},
+            "host": host}
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm
+# ---------------------------------------------------------------------------
+def stt_variant(p):
+    """The same problem with both spin-transfer torques switched on (a
+    current of 1e11 A/m^2 along x and 5e10 A/m^2 through the film plane,
+    P = 0.4, xi = 0.05, Lambda = 1, fixed layer along +z): the contexts that
+    step with the general stage kernels."""
+    for r in np.unique(p.region):
+        p.jcur[r] = (1e11, 0.0, 5e10)
+        p.xi[r] = 0.05
+        p.pol[r] = 0.4
+        p.lam[r] = 1.0
+        p.tfree[r] = p.nz * p.dz
+    p.zhang_li = True
+    p.slonczewski = True
+    return p
 
 
 def run_ours(args, rank, world, local_rank):
@@ -220,8 +376,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    def bench_workload(name, steps, warmup):
-        p = WORKLOADS[name]()
+    def timed_steps(p, steps, warmup, clocks=False):
         ctx = mm.Context.from_problem(p, device=local_rank, stream=stream.cuda_stream)
         ctx.step(warmup)
         s0 = ctx.get_stats()
@@ -230,8 +385,9 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        clocks = ClockSampler(local_rank)
-        clocks.start()
+        sampler = ClockSampler(local_rank) if clocks else None
+        if sampler:
+            sampler.start()
         with torch.cuda.stream(stream):
             for k in range(steps):
                 flush.zero_()                  # evict the previous step's data from L2
@@ -239,25 +395,67 @@ def run_ours(args, rank, world, local_rank):
                 ctx.step(1)
                 ends[k].record(stream)
         torch.cuda.synchronize()
-        clk = clocks.stop()
+        clk = sampler.stop() if sampler else None
         if world > 1:
             torch.distributed.barrier()
         dev_s = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3
         s1 = ctx.get_stats()
-        return p, ctx, dev_s, s0, s1, clk
+        return ctx, dev_s, s0, s1, clk
 
     def reduce_max(x):
         return max_over_ranks(x, world, dev)
 
     K, W = args.steps, args.warmup
-    p, ctx, dev_s, s0, s1, clk = bench_workload(args.workload, K, W)
+    p = WORKLOADS[args.workload]()
+    ctx, dev_s, s0, s1, clk = timed_steps(p, K, W, clocks=True)
     t_max = reduce_max(dev_s)
     value = whole_job_rate(p.ncells * K, world, t_max)
     attempts = (s1["accepted"] + s1["rejected"]) - (s0["accepted"] + s0["rejected"])
     launches = s1["launches"] - s0["launches"]
 
-    # demag convolution alone (the dominant kernel sequence), events on the
-    # context's stream, L2 flushed before each launch
+    # kernels of the step, one at a time with events between launches
+    # (after the timed region, continuing the same trajectory; L2 not flushed)
+    try:
+        prof = ctx.profile_attempts(args.profile_attempts)
+    except mm.MMError:   # a context outside the fused row-stage path
+        prof = []
+    kinds = {}
+    for kind, us in prof:
+        kinds.setdefault(kind, []).append(us)
+    per_kind = {k: {"launches_per_attempt": len(v), "mean_us": float(np.mean(v)), "sum_us": float(np.sum(v))}
+                for k, v in kinds.items()}
+    peaks, peak_kind = measured_peaks()
+    fp32_tflops, sms, sm_clock = mm.fp32_peak(local_rank)
+    fused_bytes, floor_bytes = yz_kernel_bytes(p)
+    _, yz_flops = demag_flops_parts(p)
+    t_yz = per_kind["yz"]["mean_us"] * 1e-6 if "yz" in per_kind else None
+    roofline = None
+    if t_yz:
+        ach = fused_bytes / t_yz / 1e9
+        roofline = {
+            "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": yz_traffic(args.workload),
+            "kernel": "(y, z) demag convolution kernel inside the RK45 step (k_yz2: y, z*K*z^-1, y^-1 fused)",
+            "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes": fused_bytes,
+            "algorithmic_basis": "five-pass bytes of the passes the kernel fuses (y, z*K*z^-1, y^-1), "
+                                 f"{fused_bytes / p.ncells:.0f} B per cell x {p.ncells} cells",
+            "avg_launch_us": round(t_yz * 1e6, 2),
+            "timing": f"CUDA events between launches on the context's stream, {args.profile_attempts} attempts "
+                      f"x {per_kind['yz']['launches_per_attempt']} launches, L2 not flushed",
+            "floor_bytes": floor_bytes, "floor_gbs": round(floor_bytes / t_yz / 1e9, 1),
+            "floor_frac": round(floor_bytes / t_yz / 1e9 / peaks["hbm_gbs"], 4),
+            "alu": {"flops": yz_flops, "achieved_tflops": round(yz_flops / t_yz / 1e12, 2),
+                    "peak_tflops": round(fp32_tflops, 1),
+                    "peak_kind": f"measured FP32 FMA throughput (mm_fp32_peak, {sms} SMs, max {sm_clock} MHz)",
+                    "frac": round(yz_flops / t_yz / 1e12 / fp32_tflops, 4)},
+        }
+    step_kernels = {"per_kind": per_kind,
+                    "sum_us_per_attempt": round(sum(us for _, us in prof), 1),
+                    "graph_us_per_attempt": round(t_max / max(attempts, 1) * 1e6, 1),
+                    "note": "events between launches remove the programmatic-dependent-launch overlap of the graph"}
+
+    # the whole convolution alone (x R2C, (y, z), x C2R kernels), L2 flushed
     m_dev = torch.tensor(p.m0.astype(np.float32), device=dev).contiguous()
     b_dev = torch.empty_like(m_dev)
     R = 50
@@ -273,23 +471,15 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
     torch.cuda.synchronize()
     conv_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / R
-    peaks, peak_kind = measured_peaks()
-    alg = algorithmic_demag_bytes(p)
-    flops = algorithmic_demag_flops(p)
-    achieved = flops / conv_s / 1e12
-    floor_gbs = alg / conv_s / 1e9
-    five_gbs = five_pass_demag_bytes(p) / conv_s / 1e9
-    roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
-                "traffic": conv_traffic(args.workload),
-                "kernel": "demag FFT convolution (x R2C, fused y/z*K*z^-1/y^-1 cluster kernel, x C2R)",
-                "algorithmic_flops": flops, "avg_launch_us": round(conv_s * 1e6, 2),
-                "peak_kind": "derived FP32 issue peak (152 SM x 128 lanes x FMA x 2.07 GHz)",
-                "hbm": {"peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
-                        "floor_bytes": alg, "floor_gbs": round(floor_gbs, 1),
-                        "floor_frac": round(floor_gbs / peaks["hbm_gbs"], 4),
-                        "five_pass_bytes": five_pass_demag_bytes(p), "five_pass_equiv_gbs": round(five_gbs, 1),
-                        "five_pass_equiv_frac": round(five_gbs / peaks["hbm_gbs"], 4)}}
+    five = five_pass_demag_bytes(p)
+    convolution = {"kernels": "k_fx_t + k_yz2 + k_ix_t (mm_demag_apply), L2 flushed before each call",
+                   "avg_us": round(conv_s * 1e6, 2), "five_pass_bytes": five,
+                   "five_pass_equiv_gbs": round(five / conv_s / 1e9, 1),
+                   "five_pass_equiv_frac": round(five / conv_s / 1e9 / peaks["hbm_gbs"], 4),
+                   "floor_bytes": algorithmic_demag_bytes(p),
+                   "floor_frac": round(algorithmic_demag_bytes(p) / conv_s / 1e9 / peaks["hbm_gbs"], 4),
+                   "flops": algorithmic_demag_flops(p),
+                   "alu_frac": round(algorithmic_demag_flops(p) / conv_s / 1e12 / fp32_tflops, 4)}
 
     # end to end through the C ABI with pinned host buffers: m up, one step,
     # m down
@@ -308,13 +498,6 @@ def run_ours(args, rank, world, local_rank):
     evals_per_step = 6.0 * attempts / K
     ctx.close()
 
-    side = None
-    if args.side and args.workload != SIDE_WORKLOAD:
-        ps, cs, ds, a0, a1, _ = bench_workload(SIDE_WORKLOAD, K, W)
-        side = {"workload": SIDE_WORKLOAD, "value": ps.ncells * K * world / reduce_max(ds), "unit": "cell-steps/s",
-                "ms_per_step": ds / K * 1e3}
-        cs.close()
-
     out = {
         "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -325,10 +508,32 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed before every timed step (256 MB write)",
                    "evals_per_step": evals_per_step, "rejected_attempts": int(s1["rejected"] - s0["rejected"])},
         "cell_evals_per_s": value * evals_per_step,
-        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roofline, "step_kernels": step_kernels, "convolution": convolution,
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
     }
-    if side:
-        out["film"] = side
+
+    if args.side and args.workload != SIDE_WORKLOAD:
+        ps = WORKLOADS[SIDE_WORKLOAD]()
+        cs, ds, _, _, _ = timed_steps(ps, K, W)
+        out["film"] = {"workload": SIDE_WORKLOAD, "value": ps.ncells * K * world / reduce_max(ds),
+                       "unit": "cell-steps/s", "ms_per_step": ds / K * 1e3}
+        cs.close()
+    if args.side:
+        general = {}
+        pg = stt_variant(WORKLOADS[DEFAULT_WORKLOAD]())
+        cg, dg, _, _, _ = timed_steps(pg, K, W)
+        general["ellipsoid_128x128x32_stt"] = {
+            "value": pg.ncells * K * world / reduce_max(dg), "unit": "cell-steps/s", "ms_per_step": dg / K * 1e3,
+            "what": "Zhang-Li + Slonczewski torques on: general stage kernels + three-kernel convolution"}
+        cg.close()
+        pf = WORKLOADS[SIDE_WORKLOAD]()
+        pf.pbc = (4, 0, 0)
+        cf, df, _, _, _ = timed_steps(pf, K, W)
+        general["grains_256x256x1_pbc_x"] = {
+            "value": pf.ncells * K * world / reduce_max(df), "unit": "cell-steps/s", "ms_per_step": df / K * 1e3,
+            "what": "periodic x (4 images each side): general stage kernels + cyclic x transform"}
+        cf.close()
+        out["general_path"] = general
     if args.batch:
         out["batch"] = run_batch(args, local_rank)
     if args.surrogate:
@@ -336,12 +541,26 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
+def _replay_instance(spec, m0, dts, m_gpu):
+    """Oracle replay of one batched instance's accepted steps (spawned
+    process): max |m_gpu - m_oracle|."""
+    from oracle.rk45 import RK45
+    from paper_1406_7635_gb300.workloads import problem_from_instance
+    p = problem_from_instance(spec, m0)
+    ora = RK45(p, m=p.m0.astype(np.float32).astype(np.float64))
+    ora.run_fixed(dts)
+    return float(np.abs(m_gpu.astype(np.float64) - ora.m).max())
+
+
+def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2, acc_per_shape=8, t_acc=5e-12):
     """The batched form: 512 independent instances of four grid sizes, each
     with its own adaptive step, advanced to t_end by one graph launch; against
     the plain single-instance path run one instance after another on a
     stratified sample (seq_per_shape instances of each grid size),
-    extrapolated by the number of instances of each size."""
+    extrapolated by the number of instances of each size.  Accuracy: the same
+    batch restarted and run to t_acc, acc_per_shape instances of each size
+    replayed by the float64 oracle with their own step sizes."""
+    import multiprocessing as mp
     import torch
     from paper_1406_7635_gb300 import mm
     from paper_1406_7635_gb300.workloads import batch_instances, problem_from_instance
@@ -360,11 +579,25 @@ def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     stats = [b.get_stats(i) for i in range(len(specs))]
-    b.close()
     cell_steps = sum(s["accepted"] * sp["nx"] * sp["ny"] * sp["nz"] for s, sp in zip(stats, specs))
     shapes = {}
     for i, sp in enumerate(specs):
         shapes.setdefault((sp["nx"], sp["ny"], sp["nz"]), []).append(i)
+    # accuracy subsample
+    for i, m in enumerate(m0s):
+        b.set_m(i, m)
+    b.set_solver()
+    b.run(t_acc)
+    sample = [i for idx in shapes.values() for i in idx[:acc_per_shape]]
+    jobs = [(specs[i], m0s[i], b.get_dt_history(i), b.get_m(i)) for i in sample]
+    b.close()
+    with single_threaded_children(), mp.get_context("spawn").Pool(min(len(jobs), host_description()["nproc"])) as pool:
+        errs = pool.starmap(_replay_instance, jobs)
+    acc = {"t_end_s": t_acc, "instances": len(sample), "max_abs_m_err": max(errs),
+           "median_abs_m_err": float(np.median(errs)), "bar": 1e-5,
+           "per_shape_max": {f"{k[0]}x{k[1]}x{k[2]}": max(e for i, e in zip(sample, errs) if i in idx[:acc_per_shape])
+                             for k, idx in shapes.items()},
+           "method": "float64 oracle replays each instance's accepted step sizes"}
     seq_time = 0.0
     for key, idx in shapes.items():
         per = []
@@ -387,7 +620,7 @@ def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2):
             "sequential_instances_per_s": len(specs) / seq_time,
             "speedup_vs_sequential": seq_time / wall,
             "sequential_sample": f"{seq_per_shape} instances per grid size, same t_end, extrapolated by count",
-            "autotuned_tiles": tiles}
+            "accuracy_vs_oracle": acc, "autotuned_tiles": tiles}
 
 
 def run_surrogate(args, local_rank, steps=40):
@@ -450,44 +683,27 @@ def run_surrogate(args, local_rank, steps=40):
             "guarded_final_m_max_err_vs_exact": float(np.abs(m_guard - m_exact).max())}
 
 
-def oracle_cpu_run(name, budget_s, max_steps, warmup=0, warmup_budget_s=30.0):
-    """The float64 oracle on the same workload: kernel set-up untimed, up to
-    `warmup` untimed adaptive RK45 steps (within warmup_budget_s), then
-    accepted steps until the time budget is spent.  Returns (problem, timed
-    steps, seconds, warm-up steps done)."""
-    from oracle.rk45 import RK45
-    p = WORKLOADS[name]()
-    s = RK45(p)
-    s.k1 = s.field.torque(s.m, 0.0)   # first stage (untimed, like the GPU's warm-up)
-    w0, done_w = time.perf_counter(), 0
-    while done_w < warmup and time.perf_counter() - w0 < warmup_budget_s:
-        s.adaptive_step()
-        done_w += 1
-    t0 = time.perf_counter()
-    steps = 0
-    while steps < max_steps:
-        s.adaptive_step()
-        steps += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return p, steps, dt, done_w
-
-
 def run_reference(args, rank, world):
+    """The float64 oracle on the host cores: one replica per core (or
+    MM_REF_CORES), each stepping the full workload, rank 0 only."""
     if rank != 0:
         return None
     budget = float(os.environ.get("MM_REF_BUDGET_S", 60))
-    p, steps, dt, warm = oracle_cpu_run(args.workload, budget, max(args.steps, 1), warmup=args.warmup)
-    v = p.ncells * steps / dt
+    host = host_description()
+    cores = int(os.environ.get("MM_REF_CORES", host["nproc"]))
+    warm = min(args.warmup, int(os.environ.get("MM_REF_WARMUP", 2)))
+    v, steps, secs = oracle_replicas(args.workload, cores, max(args.steps, 1), warmup=warm, budget_s=budget)
+    p = WORKLOADS[args.workload]()
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "cell-steps/s", "n_gpus": world,
-        "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": min(steps), "warmup": args.warmup, "ms_per_step": secs / max(min(steps), 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [p.nx, p.ny, p.nz], "cells": p.ncells},
-        "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} accepted RK45 steps of the full {args.workload} grid "
-                                   f"(float64 numpy oracle, kernel set-up untimed, ~{budget:.0f} s budget)"},
+        "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} float64 numpy oracle replicas (one thread each), {min(steps)}-"
+                                   f"{max(steps)} accepted RK45 steps each of the full {args.workload} grid after "
+                                   f"{warm} untimed warm-up steps and untimed kernel set-up (~{budget:.0f} s budget)",
+                         "host": host},
         "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -500,6 +716,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=10, help="accepted oracle steps per replica (cpu_baseline)")
+    ap.add_argument("--profile-attempts", type=int, default=10, help="attempts launched kernel by kernel")
     ap.add_argument("--no-side", dest="side", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false")
@@ -519,11 +737,7 @@ def main():
         return
     out = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        budget = float(os.environ.get("MM_CPU_BUDGET_S", 20))
-        p, steps, dt, _ = oracle_cpu_run(args.workload, budget, 1000)
-        out["cpu_baseline"] = {"value": p.ncells * steps / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                               "sample": f"{steps} accepted RK45 steps of the full {args.workload} grid "
-                                         f"(float64 numpy oracle, kernel set-up untimed)"}
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_steps, host_description()["nproc"])
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -162,6 +162,20 @@ int mm_set_solver(mm_ctx* ctx, double max_err, double headroom, double dt0,
  * stepping.  The array is copied. */
 int mm_set_fixed_dt_sequence(mm_ctx* ctx, const double* dts, int n);
 
+/* Failure detection (no counterpart in the paper): the row-stage kernels wait
+ * for their tensor copies (TMA) on mbarriers, and every such wait is bounded.
+ * `cycles` is the limit in SM clock cycles (default 2^30, about half a second
+ * at 2.07 GHz); a wait that reaches it records MM_ERR_TIMEOUT in the device
+ * state and the attempt is abandoned: the kernel first waits, with the
+ * default limit, for its copies still in flight, then returns, and the later
+ * kernels of the attempt skip their work.  mm_step / mm_run then return
+ * MM_ERR_TIMEOUT with m, t and dt as they were before the abandoned attempt,
+ * and the context stays usable.  0 gives up at the first wait without polling
+ * (it exercises that error path; copies are never lost).  The limit is part of
+ * the device state (kept in checkpoints).  MM_ERR_ARG if cycles < 0. */
+int mm_set_wait_limit(mm_ctx* ctx, long long cycles);
+int mm_get_wait_limit(mm_ctx* ctx, long long* cycles);
+
 /* Integrator (Sec. IV "Dynamics"): MM_RK45, Dormand-Prince 5(4), 6 new
  * torque evaluations per attempt (default); MM_RK23, Bogacki-Shampine 3(2),
  * 3 per attempt, step factor exponent 1/3.  Both reuse the last stage as the
@@ -239,21 +253,56 @@ int mm_demag_apply(mm_ctx* ctx, const float* m, float* b);
  * for repeated use on one grid).
  *  - M, B: device pointers on the current device, float32 SoA [3][nz][ny][nx];
  *    the caller owns them.  stream: a cudaStream_t, or NULL.
- *  - Scratch: one static device array of 32 MiB per GPU that loads the
- *    library, held until the process exits.  Grids whose kernel precompute,
- *    kernel spectrum and FFT spectrum do not fit (about 2.4 M padded points in
- *    2-D, fewer in 3-D) are rejected with MM_ERR_ARG and a message giving the
- *    bytes needed.  The first call on a device looks up the array's device
- *    address (cudaGetSymbolAddress); make that first call before capturing
- *    any stream on that device.
- *  - Every call uses the same array and leaves its contents behind; calls
- *    that overlap on the GPU (other streams, other threads) race.  The call
- *    returns after the stream has finished.  Calls no cudaMalloc/cudaFree. */
+ *  - Scratch: one static device array of 32 MiB (33 554 432 bytes) per GPU
+ *    that loads the library, held until the process exits.  A grid needs
+ *    16 KB of tables + 2 bytes per cell + the float32 kernel octant (24 B per
+ *    point of (px/2+1)(py/2+1)(pz/2+1)) + the spectrum (24 B per point of
+ *    nz * (py if nz > 1 else ny) * hxs, hxs = px/2+1 rounded up to 8) + two
+ *    float64 precompute areas (48 B per point of the largest of n,
+ *    (px/2+1) ny nz, (px/2+1)(py/2+1) nz and the octant) + a small table,
+ *    each rounded up to 256 bytes (px, py, pz: the padded sizes, the power of
+ *    two >= 2n - 1).  So 512x256x1, 384x256x1 and 64x64x32 fit, while
+ *    512x512x1, 1024x256x1, 128x64x32 and 128x128x16 do not.  A grid that
+ *    does not fit is rejected with MM_ERR_ARG and a message giving the bytes
+ *    it needs, before any device call.
+ *  - The first call on a device (and the first after that device's context
+ *    was re-created) looks up the array's device address with that device
+ *    current (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - Every call uses the same array and leaves its contents behind (each call
+ *    re-initialises what it reads); calls that overlap on the GPU (other
+ *    streams, other threads) race.  The call synchronises `stream` before it
+ *    returns.  It calls no cudaMalloc, cudaFree or allocating library
+ *    routine. */
 int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
                            const float* M, float* B, void* stream);
 
 /* Blocks until the context's stream is idle. */
 int mm_sync(mm_ctx* ctx);
+
+/* Measurement of the stepping kernels (no counterpart in the paper).  Runs
+ * `attempts` RK45 attempts from the current state, as mm_step(attempts)
+ * would (each accepted or rejected by the controller), launched one kernel
+ * at a time with a CUDA event recorded on the context's stream after each
+ * launch instead of replaying the attempt's graph.  For each launch position
+ * of one attempt (*n_out of them, at most max) it writes the kernel kind
+ * (kinds[i]: 0 stage-input prep, 1 (y, z) demag convolution kernel, 2
+ * row-stage kernel: x transforms, field, torque, stage update) and its mean
+ * duration over the attempts in microseconds (us[i]).  The events keep each
+ * kernel from overlapping its neighbour (no programmatic-dependent-launch
+ * overlap), so the sum can exceed the graph's time per attempt.  L2 is not
+ * flushed between launches.  MM_ERR_STATE before set_m and unless the context
+ * steps with the fused row-stage kernels (RK45, exact demag, no periodic x
+ * axis, no spin-transfer torque); the controller's errors as mm_step. */
+int mm_profile_attempts(mm_ctx* ctx, int attempts, int max, int* kinds, double* us, int* n_out);
+
+/* FP32 fused multiply-add throughput of `device` (no counterpart in the
+ * paper; the ALU roof of the convolution's arithmetic): a kernel of
+ * independent FMA chains on every SM, timed with CUDA events on an internal
+ * stream (best of `reps` launches after one warm-up).  *tflops receives
+ * 2 x FMAs / time in TFLOP/s; *sm_count the device's multiprocessors and
+ * *clock_mhz its maximum SM clock (may be NULL).  MM_ERR_ARG for reps < 1. */
+int mm_fp32_peak(int device, int reps, double* tflops, int* sm_count, int* clock_mhz);
 
 /* ---- Learned demag surrogate ----------------------------------------------
  * A Fourier-neural-operator approximation of the demag field of a 2-D film
@@ -356,6 +405,15 @@ int mm_batch_num_classes(mm_batch* b);
  * (may be NULL) = the chosen convolution's time for all the class's
  * instances in microseconds. */
 int mm_batch_class_info(mm_batch* b, int c, int info[7], double* conv_us);
+/* Pins the FFT tiles of class c instead of the autotuner's choice (for
+ * reproducible timings and tests): (cly, clz) must be one of the residue
+ * splits the class's fused plan offers (each of 1 or 2, py/cly >= ny,
+ * pz/clz >= nz, at most 4096 points per block) and xrows one of the offered
+ * x-row block sizes (the default rule, half or twice it); MM_ERR_ARG
+ * otherwise.  Takes effect at the next mm_batch_run (the run's graph is
+ * captured again); the result differs from the autotuned tiles' only by
+ * float32 rounding. */
+int mm_batch_set_tiles(mm_batch* b, int c, int cly, int clz, int xrows);
 
 #ifdef __cplusplus
 }

@@ -736,6 +736,28 @@ int mm_batch_get_dt_history(mm_batch* B, int i, double* dts, int max, int* n) {
 
 int mm_batch_num_classes(mm_batch* B) { return B ? (int)B->cls.size() : 0; }
 
+int mm_batch_set_tiles(mm_batch* B, int c, int cly, int clz, int xrows) {
+  if (!B || c < 0 || c >= (int)B->cls.size()) return bfail(MM_ERR_ARG, "bad batch or class index");
+  BClass& C = B->cls[c];
+  int sp[4][2];
+  const int nsp = fused_splits(C.g, sp, 4);
+  bool ok_split = false;
+  for (int i = 0; i < nsp; ++i) ok_split = ok_split || (sp[i][0] == cly && sp[i][1] == clz);
+  int xr[3];
+  const int nxr = fused_xrows(C.g, xr, 3);
+  bool ok_rows = false;
+  for (int i = 0; i < nxr; ++i) ok_rows = ok_rows || xr[i] == xrows;
+  if (!ok_split || !ok_rows) return bfail(MM_ERR_ARG, "tiles not offered for this shape class");
+  fused_set_split(C.g, cly, clz);
+  C.g.xrows = xrows;
+  // the captured graph holds the old tiles: capture again at the next run
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  return MM_OK;
+}
+
 int mm_batch_class_info(mm_batch* B, int c, int info[7], double* conv_us) {
   if (!B || !info || c < 0 || c >= (int)B->cls.size()) return bfail(MM_ERR_ARG, "bad batch or class index");
   const BClass& C = B->cls[c];

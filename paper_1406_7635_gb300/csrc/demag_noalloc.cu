@@ -27,10 +27,34 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device, looked up once with that device
-// current (the host-side symbol is a stand-in, not a device address).
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+// Device address of g_scratch per device (the host-side symbol is a
+// stand-in, not a device address), looked up with that device current and
+// kept with the context it belongs to: a device whose primary context was
+// torn down and re-created (cudaDeviceReset) reloads the module, and the
+// address is looked up again.
+struct ScratchSlot {
+  CUcontext ctx;
+  unsigned char* ptr;
+};
+ScratchSlot g_scratch_slot[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+// the calling thread's current context through the runtime's driver entry
+// point (no link against the driver library); null when unavailable
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CUcontext current_context() {
+  static const CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<CtxGetCurrentFn>(f);
+    return CtxGetCurrentFn(nullptr);
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 int noalloc_fail(int code, const std::string& msg) {
   mm::set_last_error(msg);
@@ -53,12 +77,6 @@ __global__ void k_noalloc_lut(mm::RegionLUT* lut) {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-int next_pow2(int v) {
-  int p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
-
 }  // namespace
 
 extern "C" int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, const float* M,
@@ -67,25 +85,10 @@ extern "C" int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double 
   if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 512 || nz > 512)
     return noalloc_fail(MM_ERR_ARG, "grid sizes must be 1..1024 (x), 1..512 (y, z)");
   if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return noalloc_fail(MM_ERR_ARG, "cell sizes must be > 0");
-  mm::Geom g{};
-  g.nx = nx;
-  g.ny = ny;
-  g.nz = nz;
-  g.n = (long long)nx * ny * nz;
-  g.idx2 = (float)(1.0 / (dx * dx));
-  g.idy2 = (float)(1.0 / (dy * dy));
-  g.idz2 = (float)(1.0 / (dz * dz));
-  g.px = nx == 1 ? 1 : next_pow2(2 * nx - 1);
-  g.py = ny == 1 ? 1 : next_pow2(2 * ny - 1);
-  g.pz = nz == 1 ? 1 : next_pow2(2 * nz - 1);
-  g.lx = g.px == 1 ? 1 : g.px / 2;
-  g.hx = g.px == 1 ? 1 : g.lx + 1;
-  g.hxs = (g.hx + 7) / 8 * 8;
-  g.srows = g.pz > 1 ? g.py : ny;
-  g.sc = (long long)nz * g.srows * g.hxs;
-  g.hkx = g.px == 1 ? 1 : g.px / 2 + 1;
-  g.hky = g.py == 1 ? 1 : g.py / 2 + 1;
-  g.hkz = g.pz == 1 ? 1 : g.pz / 2 + 1;
+  // the context path's geometry (padding, spectrum strides, octant sizes);
+  // the fused-convolution fields stay zero, so the general five-pass
+  // convolution runs
+  const mm::Geom g = mm::make_geom(nx, ny, nz, dx, dy, dz);
 
   // carve the scratch array
   const size_t b_tw = align256(2048 * sizeof(float2));
@@ -110,15 +113,19 @@ extern "C" int mm_demag_field_noalloc(int nx, int ny, int nz, double dx, double 
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(MM_ERR_ARG, "device index out of range");
   unsigned char* base = nullptr;
   {
-    // set-up, once per device, with that device current
+    // set-up, once per device (and again after that device's context was
+    // re-created), with that device current
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot& slot = g_scratch_slot[dev];
+    const CUcontext cur = current_context();
+    if (!slot.ptr || !cur || cur != slot.ctx) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_scratch);
       if (e != cudaSuccess) return noalloc_fail(MM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+      slot.ptr = static_cast<unsigned char*>(p);
+      slot.ctx = current_context();
     }
-    base = g_scratch_ptr[dev];
+    base = slot.ptr;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   size_t off = 0;

@@ -286,11 +286,9 @@ template <int L, int MODE, int AXIS>
 void run_col(const Geom& g, const Buffers& b, cudaStream_t s) {
   using C = ColCfg<L>;
   auto kern = k_col<L, MODE, AXIS, C::TK, C::NT>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    attr_set = true;
-  }
+  // (a function attribute belongs to the current device's context: set on
+  // every launch, a host-side call that enqueues nothing)
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   const int others = AXIS == 1 ? g.nz : g.py;
   dim3 grid((g.hx + C::TK - 1) / C::TK, others);
   kern<<<grid, C::NT, C::SMEM, s>>>(g, b.spec, b.kt, b.tw, b.st);

@@ -679,16 +679,13 @@ struct YzCfg {
 };
 
 // one cluster launch of a (y, z) kernel: CLY*CLZ blocks per kx plane and
-// instance; the kernel's shared-memory limit is raised on its first launch
-// (outside stream capture: the context's warm-up and the batch autotuner
-// launch every configuration first)
+// instance; the kernel's shared-memory limit is set on every launch (a
+// function attribute belongs to the current device's context; the call is
+// host-side and enqueues nothing)
 template <typename K>
-void launch_yz_cluster(K kern, bool& attr_set, size_t smem, int nt, const Geom& g, const Buffers& b, cudaStream_t s,
+void launch_yz_cluster(K kern, size_t smem, int nt, const Geom& g, const Buffers& b, cudaStream_t s,
                        const BatchArgs& ba, bool pdl) {
-  if (!attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int CL = g.cly * g.clz;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(g.hx * CL * ba.count);
@@ -713,13 +710,11 @@ void run_yz(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba
   if constexpr (LZ >= 4) {
     // z-split clusters share the y transforms between the two z classes
     if (g.clz == 2) {
-      static bool set2 = false;
-      launch_yz_cluster(k_yz2<LY, LZ, C::NT>, set2, C::SMEM, C::NT, g, b, s, ba, pdl);
+      launch_yz_cluster(k_yz2<LY, LZ, C::NT>, C::SMEM, C::NT, g, b, s, ba, pdl);
       return;
     }
   }
-  static bool set1 = false;
-  launch_yz_cluster(k_yz<LY, LZ, C::NT>, set1, C::SMEM, C::NT, g, b, s, ba, pdl);
+  launch_yz_cluster(k_yz<LY, LZ, C::NT>, C::SMEM, C::NT, g, b, s, ba, pdl);
 }
 
 __global__ void k_kt_transpose(Geom g, const float* __restrict__ kt, float* __restrict__ ktf) {

@@ -282,6 +282,9 @@ int build_graph(mm_ctx* c) {
 int status_to_code(int status) {
   if (status == MM_ERR_NONFINITE) return fail(MM_ERR_NONFINITE, "non-finite step error (NaN/Inf in m or torque)");
   if (status == MM_ERR_DT_UNDERFLOW) return fail(MM_ERR_DT_UNDERFLOW, "time step fell below dt_min");
+  if (status == MM_ERR_TIMEOUT)
+    return fail(MM_ERR_TIMEOUT, "a kernel's bounded wait on its tensor copies expired (the attempt was abandoned; m, t "
+                                "and dt are those before it)");
   if (status != 0) return fail(status, "device status error");
   return MM_OK;
 }
@@ -479,6 +482,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   s.dt_max = 1e-10;
   s.precession = 1;
   s.done = 1;
+  s.wait_cycles = kWaitCycles;
   int rc = write_state(c);
   if (rc) return cleanup(rc);
   rc = flush_luts(c);
@@ -667,6 +671,23 @@ int mm_set_solver(mm_ctx* c, double max_err, double headroom, double dt0, double
   s.dt_min = dt_min;
   s.dt_max = dt_max;
   return write_state(c);
+}
+
+int mm_set_wait_limit(mm_ctx* c, long long cycles) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (cycles < 0) return fail(MM_ERR_ARG, "the wait limit must be >= 0 cycles");
+  int rc = read_state(c);
+  if (rc) return rc;
+  c->st_host->wait_cycles = cycles;
+  return write_state(c);
+}
+
+int mm_get_wait_limit(mm_ctx* c, long long* cycles) {
+  if (!c || !cycles) return fail(MM_ERR_ARG, "ctx and cycles must not be NULL");
+  int rc = current_state(c);
+  if (rc) return rc;
+  *cycles = c->st_host->wait_cycles;
+  return MM_OK;
 }
 
 int mm_set_fixed_dt_sequence(mm_ctx* c, const double* dts, int n) {
@@ -1288,6 +1309,75 @@ int mm_sync(mm_ctx* c) {
   if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
   MM_CUDA(cudaStreamSynchronize(c->stream));
   return MM_OK;
+}
+
+int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us, int* n_out) {
+  if (!c || attempts < 1 || max < 1 || !kinds || !us || !n_out) return fail(MM_ERR_ARG, "bad profiling arguments");
+  if (!c->m_set) return fail(MM_ERR_STATE, "m has not been set");
+  if (!rowstage_path(c)) return fail(MM_ERR_STATE, "profiling covers the fused row-stage path only");
+  int rc = flush_luts(c);
+  if (rc) return rc;
+  // launch positions of one attempt: the prep kernel, then per stage the
+  // (y, z) kernel (with demag) and the row kernel
+  std::vector<int> kind;
+  kind.push_back(0);
+  for (int s = 1; s < 7; ++s) {
+    if (c->T.demag) kind.push_back(1);
+    kind.push_back(2);
+  }
+  const int P = (int)kind.size();
+  std::vector<cudaEvent_t> ev((size_t)P * attempts + 1, nullptr);
+  auto destroy = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  for (auto& e : ev) {
+    const cudaError_t er = cudaEventCreate(&e);
+    if (er != cudaSuccess) {
+      destroy();
+      return fail(MM_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(er));
+    }
+  }
+  c->st_fresh = false;
+  launch_begin_mode(c->b, 0, attempts, 0.0, c->stream);
+  c->launches += 1;
+  const bool k1_was_valid = c->k1_valid;
+  if (!c->k1_valid) enqueue_k1(c);
+  size_t q = 0;
+  cudaError_t e = cudaEventRecord(ev[q++], c->stream);
+  for (int a = 0; a < attempts && e == cudaSuccess; ++a) {
+    launch_rowstage(c->g, c->b, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
+    e = cudaEventRecord(ev[q++], c->stream);
+    for (int s = 1; s < 7 && e == cudaSuccess; ++s) {
+      if (c->T.demag) {
+        launch_demag_yz(c->g, c->b, c->stream);
+        e = cudaEventRecord(ev[q++], c->stream);
+      }
+      launch_rowstage(c->g, c->b, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[q++], c->stream);
+    }
+  }
+  c->launches += (long long)attempts * P;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  std::vector<double> sum(P, 0.0);
+  for (size_t i = 1; i < q && e == cudaSuccess; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+    sum[(i - 1) % P] += ms * 1e3;
+  }
+  destroy();
+  if (e != cudaSuccess) return fail(MM_ERR_CUDA, std::string("profiled attempts: ") + cudaGetErrorString(e));
+  rc = read_state(c);
+  if (rc) return rc;
+  c->k1_valid = k1_was_valid || c->st_host->call_attempts > 0;
+  const int n = std::min(P, max);
+  for (int i = 0; i < n; ++i) {
+    kinds[i] = kind[i];
+    us[i] = sum[i] / attempts;
+  }
+  *n_out = n;
+  return status_to_code(c->st_host->status);
 }
 
 }  // extern "C"

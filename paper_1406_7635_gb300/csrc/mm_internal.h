@@ -117,7 +117,11 @@ struct DevState {
   int call_attempts;         // attempts since the last begin
   int precession;
   int method;               // 0 Dormand-Prince RK45, 1 Bogacki-Shampine RK23
+  long long wait_cycles;    // limit of a kernel's wait on its tensor copies (SM clock cycles)
 };
+
+// default wait limit: 2^30 cycles, about half a second at the maximum SM clock
+constexpr long long kWaitCycles = 1LL << 30;
 
 struct Buffers {
   float* m[2];        // current / candidate m (parity)

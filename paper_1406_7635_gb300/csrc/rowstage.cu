@@ -69,12 +69,15 @@ __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Waits for phase 0 of bar to complete; false after about 2^30 cycles
-// (half a second), so that a lost transfer ends the kernel with an error
-// instead of a hang.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar) {
+// Waits for phase 0 of bar to complete; false once `limit` SM cycles have
+// passed (the context's wait limit, by default 2^30 cycles: half a second),
+// so that a lost transfer ends the kernel with an error instead of a hang.
+// The limit is checked before each poll: with limit 0 the wait gives up
+// without polling.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, long long limit) {
   const long long t0 = clock64();
   for (;;) {
+    if (clock64() - t0 >= limit) return false;
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -82,7 +85,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar) {
         : "r"(smem_u32(bar))
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1LL << 30)) return false;
   }
 }
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -450,15 +452,18 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   // unless SL; only the stencil group may stay in flight)
   if constexpr (TT || !SL) asm volatile("cp.async.wait_all;\n" ::: "memory");
   else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  // (a wait that gives up records MM_ERR_TIMEOUT and ends the attempt; the
+  // copies still in flight are then awaited with the default limit, so that
+  // they land before the block's shared memory is released)
   if constexpr (SL) {
-    if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[0]);
+    if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[0], st->wait_cycles);
     __syncthreads();
     if (!tma_ok) {   // uniform; the copies in flight land before the block ends
       if (threadIdx.x == 0) {
         st->status = -6;   // MM_ERR_TIMEOUT
         st->done = 1;
-        mbar_wait(&bars[0]);
-        if (TT) mbar_wait(&bars[1]);
+        mbar_wait(&bars[0], kWaitCycles);
+        if (TT) mbar_wait(&bars[1], kWaitCycles);
       }
       return;
     }
@@ -488,13 +493,13 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   // (outputs 2n >= nx are cropped: the field code reads x < nx)
   FftX<L, 1, 3 * ROWS, NT, LIn, LIn, Bl, L>::run(sm, twl, L, (g.nx + 1) / 2);
   if constexpr (TT) {
-    if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[1]);
+    if (threadIdx.x == 0) tma_ok = mbar_wait(&bars[1], st->wait_cycles);
     __syncthreads();
     if (!tma_ok) {
       if (threadIdx.x == 0) {
         st->status = -6;   // MM_ERR_TIMEOUT
         st->done = 1;
-        mbar_wait(&bars[1]);
+        mbar_wait(&bars[1], kWaitCycles);
       }
       return;
     }
@@ -794,16 +799,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // (a function-local static: initialised once, thread-safe)
+  static const EncodeTiledFn fn = [] {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(f);
-  }
+      return reinterpret_cast<EncodeTiledFn>(f);
+    return EncodeTiledFn(nullptr);
+  }();
   return fn;
 }
 

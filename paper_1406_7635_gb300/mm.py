@@ -79,6 +79,8 @@ _SIGS = {
     "mm_get_m_device": (_I, [_P, _P]),
     "mm_set_solver": (_I, [_P, _D, _D, _D, _D, _D]),
     "mm_set_fixed_dt_sequence": (_I, [_P, _P, _I]),
+    "mm_set_wait_limit": (_I, [_P, C.c_longlong]),
+    "mm_get_wait_limit": (_I, [_P, C.POINTER(C.c_longlong)]),
     "mm_step": (_I, [_P, _I]),
     "mm_run": (_I, [_P, _D]),
     "mm_get_time": (_I, [_P, C.POINTER(_D), C.POINTER(_D)]),
@@ -102,6 +104,8 @@ _SIGS = {
     "mm_demag_apply": (_I, [_P, _P, _P]),
     "mm_demag_field_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _P, _P, _P]),
     "mm_sync": (_I, [_P]),
+    "mm_profile_attempts": (_I, [_P, _I, _I, _P, _P, C.POINTER(_I)]),
+    "mm_fp32_peak": (_I, [_I, _I, C.POINTER(_D), C.POINTER(_I), C.POINTER(_I)]),
     "mm_batch_create": (_I, [C.POINTER(_P), _I, C.POINTER(mm_instance_spec), _I, _P]),
     "mm_batch_destroy": (_I, [_P]),
     "mm_batch_set_m": (_I, [_P, _I, _P]),
@@ -112,6 +116,7 @@ _SIGS = {
     "mm_batch_get_dt_history": (_I, [_P, _I, _P, _I, C.POINTER(_I)]),
     "mm_batch_num_classes": (_I, [_P]),
     "mm_batch_class_info": (_I, [_P, _I, _P, C.POINTER(_D)]),
+    "mm_batch_set_tiles": (_I, [_P, _I, _I, _I, _I]),
     "mm_fno_create": (_I, [C.POINTER(_P), _I, _I, C.POINTER(mm_fno_cfg), _I, _P]),
     "mm_fno_destroy": (_I, [_P]),
     "mm_fno_param_count": (C.c_longlong, [_P]),
@@ -157,6 +162,17 @@ def demag_field_noalloc(M_dev, B_dev, nx, ny, nz, dx, dy, dz, stream=None):
     static scratch: no device allocation (see mm_demag_field_noalloc)."""
     _check(mm_demag_field_noalloc(nx, ny, nz, dx, dy, dz, C.c_void_p(M_dev.data_ptr()),
                                   C.c_void_p(B_dev.data_ptr()), stream))
+
+
+def fp32_peak(device=0, reps=5):
+    """Measured FP32 FMA throughput (TFLOP/s), SM count and maximum SM clock
+    (MHz) of a device (mm_fp32_peak)."""
+    tf, sms, mhz = C.c_double(), C.c_int(), C.c_int()
+    _check(mm_fp32_peak(device, reps, C.byref(tf), C.byref(sms), C.byref(mhz)))
+    return tf.value, sms.value, mhz.value
+
+
+KERNEL_KINDS = {0: "prep", 1: "yz", 2: "row"}
 
 
 class Context:
@@ -222,6 +238,14 @@ class Context:
     def set_fixed_dt_sequence(self, dts):
         a = np.ascontiguousarray(dts, dtype=np.float64)
         _check(mm_set_fixed_dt_sequence(self.h, _ptr(a) if a.size else None, a.size))
+
+    def set_wait_limit(self, cycles):
+        _check(mm_set_wait_limit(self.h, int(cycles)))
+
+    def get_wait_limit(self):
+        v = C.c_longlong()
+        _check(mm_get_wait_limit(self.h, C.byref(v)))
+        return v.value
 
     # --- state ---
     def set_m(self, m):
@@ -333,6 +357,17 @@ class Context:
 
     def sync(self):
         _check(mm_sync(self.h))
+
+    def profile_attempts(self, attempts):
+        """Per launch position of one RK45 attempt: (kind, mean microseconds)
+        over `attempts` attempts launched one kernel at a time with events
+        between them (mm_profile_attempts); the state advances as by
+        step(attempts)."""
+        kinds = np.zeros(64, dtype=np.int32)
+        us = np.zeros(64, dtype=np.float64)
+        n = C.c_int()
+        _check(mm_profile_attempts(self.h, int(attempts), 64, _ptr(kinds), _ptr(us), C.byref(n)))
+        return [(KERNEL_KINDS[int(k)], float(u)) for k, u in zip(kinds[:n.value], us[:n.value])]
 
     def set_demag_surrogate(self, net, ms_ref, check_every=10, fallback_rel_err=1e-3):
         _check(mm_set_demag_surrogate(self.h, None if net is None else net.h, ms_ref, check_every,
@@ -449,6 +484,11 @@ class Batch:
 
     def num_classes(self):
         return mm_batch_num_classes(self.h)
+
+    def set_tiles(self, c, cly, clz, xrows):
+        """Pin the FFT tiles of shape class c (one of the offered splits and
+        x-row block sizes)."""
+        _check(mm_batch_set_tiles(self.h, int(c), int(cly), int(clz), int(xrows)))
 
 
 class FNO:

@@ -115,3 +115,45 @@ def test_autotuned_tiles_are_valid(batch_run):
         default = 2 if lx >= 512 else (4 if lx >= 256 else 8)
         assert t["xrows"] in (max(default // 2, 1), default, 2 * default)
         assert t["conv_us"] > 0
+
+
+# The batched workload's own shape classes (128 x 64 x 2 and 96 x 96 x 4, 4 nm
+# cells), each run with every residue split its fused plan offers, pinned in
+# turn: no split (one block per kx plane), y split, z split (the shared-y
+# cluster kernel for 96 x 96 x 4) and both.
+C4_SHAPES = ((128, 64, 2), (96, 96, 4))
+
+
+@pytest.mark.parametrize("split", [(1, 1), (2, 1), (1, 2), (2, 2)])
+def test_c4_shape_classes_every_split_vs_oracle(mm, split):
+    specs, m0s = batch_instances(4, shapes=C4_SHAPES, seed=91)
+    b = mm.Batch(specs)
+    assert b.num_classes() == 2
+    for c in range(b.num_classes()):
+        info = b.class_info(c)
+        b.set_tiles(c, split[0], split[1], info["xrows"])
+        pinned = b.class_info(c)
+        assert (pinned["cly"], pinned["clz"]) == split
+    for i, m in enumerate(m0s):
+        b.set_m(i, m)
+    t_end = 2e-12
+    b.run(t_end)
+    for i in range(len(specs)):
+        st = b.get_stats(i)
+        assert st["status"] == 0 and st["t"] == t_end
+        p = problem_from_instance(specs[i], m0s[i])
+        ora = RK45(p, m=p.m0.astype(np.float32).astype(np.float64))
+        ora.run_fixed(b.get_dt_history(i))
+        assert np.abs(b.get_m(i).astype(np.float64) - ora.m).max() <= M_TOL
+    b.close()
+
+
+def test_set_tiles_rejects_splits_the_plan_does_not_offer(mm):
+    specs, m0s = batch_instances(2, shapes=((32, 32, 1),), seed=3)
+    b = mm.Batch(specs)
+    info = b.class_info(0)
+    with pytest.raises(mm.MMError):
+        b.set_tiles(0, 1, 2, info["xrows"])     # a 2-D grid has no z split
+    with pytest.raises(mm.MMError):
+        b.set_tiles(0, 1, 1, 3)                 # not an offered x-row block size
+    b.close()

@@ -100,6 +100,65 @@ def test_forward_and_gradients_vs_oracle(mm, S, C, L, H, W, Mx, My):
     net.close()
 
 
+# The benchmark's network: width 32, 4 layers, 24 x modes and 24 + 24 y modes,
+# on a 64 x 96 film (the fused width-32 layer kernel, the width-32 pointwise
+# lift and projection, split-K slices of the x products).  The oracle runs
+# once per sample for both batch sizes.
+WIDE = dict(C=32, L=4, H=64, W=96, Mx=24, My=24)
+
+
+@pytest.fixture(scope="module")
+def wide_oracle():
+    C, L, H, W, Mx, My = (WIDE[k] for k in ("C", "L", "H", "W", "Mx", "My"))
+    rng = np.random.default_rng(32)
+    params = init_params(C, L, Mx, My, seed=8)
+    for k in list(params):
+        if k.startswith("b") or k in ("p", "q"):
+            params[k] = 0.1 * rng.standard_normal(params[k].shape)
+    mats = dft_mats(H, W, Mx, My)
+    u = rng.standard_normal((2, 3, H, W))
+    y = rng.standard_normal((2, 3, H, W))
+    yh = [forward(params, u[s], L, mats) for s in range(2)]
+    g = [backward(params, yh[s][1], yh[s][0], y[s], L, mats) for s in range(2)]
+    return params, u, y, [a[0] for a in yh], g
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_benchmark_width_forward_and_gradients_vs_oracle(mm, wide_oracle, S):
+    C, L, H, W, Mx, My = (WIDE[k] for k in ("C", "L", "H", "W", "Mx", "My"))
+    params, u, y, yh, gs = wide_oracle
+    u, y = u[:S], y[:S]
+    ysq = float(np.sum(y * y))
+    oracle_loss = sum(float(np.sum((yh[s] - y[s]) ** 2)) for s in range(S)) / ysq
+    grads = None
+    for s in range(S):
+        scale = float(np.sum(y[s] * y[s])) / ysq   # per-sample normalisation -> the batch sum
+        g = {k: v * scale for k, v in gs[s].items()}
+        grads = g if grads is None else {k: grads[k] + g[k] for k in g}
+    g_ora = flatten(grads, L)
+    net = mm.FNO(H, W, width=C, layers=L, modes_x=Mx, modes_y=My, max_batch=S)
+    net.set_params(flatten(params, L).astype(np.float32))
+    ud = torch.tensor(u.astype(np.float32), device="cuda").contiguous()
+    yd = torch.tensor(y.astype(np.float32), device="cuda").contiguous()
+    out = torch.empty_like(ud)
+    net.forward(ud, out, S)
+    y_gpu = out.cpu().numpy().astype(np.float64)
+    y_ora = np.stack(yh[:S])
+    assert rel(y_gpu, y_ora) < 2e-2
+    assert cosine(y_gpu.ravel(), y_ora.ravel()) >= 0.999
+    g_gpu, l_gpu = net.grad(ud, yd, S)
+    assert abs(l_gpu - oracle_loss) < 2e-2 * oracle_loss
+    off = 0
+    for name, size in [("P", C * 3), ("p", C)] + sum(
+            [[(f"W{l}", C * C), (f"b{l}", C), (f"R{l}", 2 * C * C * 2 * My * Mx)] for l in range(L)], []) + [
+            ("Q", 3 * C), ("q", 3)]:
+        a, b = g_gpu[off:off + size].astype(np.float64), g_ora[off:off + size]
+        off += size
+        assert cosine(a, b) >= 0.999, name
+        assert rel(a, b) <= 2e-2, name
+    net.close()
+
+
 def test_training_on_exact_trajectories_reduces_loss(mm):
     p = film_sp4(64, 64)
     ctx = mm.Context.from_problem(p)
