@@ -286,15 +286,31 @@ int mm_sync(mm_ctx* ctx);
  * at a time with a CUDA event recorded on the context's stream after each
  * launch instead of replaying the attempt's graph.  For each launch position
  * of one attempt (*n_out of them, at most max) it writes the kernel kind
- * (kinds[i]: 0 stage-input prep, 1 (y, z) demag convolution kernel, 2
- * row-stage kernel: x transforms, field, torque, stage update) and its mean
- * duration over the attempts in microseconds (us[i]).  The events keep each
+ * (kinds[i]: 0 stage-input prep, 1 (y, z) demag convolution cluster kernel,
+ * 2 row-stage kernel: x transforms, field, torque, stage update; with the
+ * three-kernel (y, z) path 3 y forward, 4 column kernel: z forward, kernel
+ * product, z inverse, 5 y inverse) and its mean duration over the attempts
+ * in microseconds (us[i]).  The events keep each
  * kernel from overlapping its neighbour (no programmatic-dependent-launch
  * overlap), so the sum can exceed the graph's time per attempt.  L2 is not
  * flushed between launches.  MM_ERR_STATE before set_m and unless the context
  * steps with the fused row-stage kernels (RK45, exact demag, no periodic x
  * axis, no spin-transfer torque); the controller's errors as mm_step. */
 int mm_profile_attempts(mm_ctx* ctx, int attempts, int max, int* kinds, double* us, int* n_out);
+
+/* How the (y, z) part of the demag convolution (Sec. III.B) runs on a grid
+ * with the fused spectrum layout (no counterpart in the paper; both compute
+ * the same convolution, up to float32 rounding): which = 0 the grid's
+ * default (2 where available, else 1), 1 one thread-block cluster per kx
+ * plane (the (ky, kz) plane split into frequency residue classes across the
+ * cluster's blocks, summed through distributed shared memory), 2 three
+ * kernels over a y-transformed buffer of 24 B per (kx, z, ky) point (y
+ * forward; per (kx, ky) column z forward, kernel product and z inverse;
+ * y inverse).  2 needs open y and z axes, py >= 32 and 16 <= pz <= 64
+ * (MM_ERR_ARG otherwise).  *active (may be NULL) receives the kernels in use:
+ * 1 or 2, or 0 on a grid without the fused layout.  The stepping graph is
+ * captured again at the next step. */
+int mm_set_yz_kernels(mm_ctx* ctx, int which, int* active);
 
 /* FP32 fused multiply-add throughput of `device` (no counterpart in the
  * paper; the ALU roof of the convolution's arithmetic): a kernel of

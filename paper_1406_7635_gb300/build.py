@@ -14,7 +14,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["demag_tensor.cu", "fft_conv.cu", "fft_fused.cu", "llg.cu", "mm_api.cu", "demag_noalloc.cu", "batch.cu", "fno.cu", "rowstage.cu", "peak.cu"]
+UNITS = ["demag_tensor.cu", "fft_conv.cu", "fft_fused.cu", "llg.cu", "mm_api.cu", "demag_noalloc.cu", "batch.cu", "fno.cu", "rowstage.cu", "peak.cu", "fft_yz3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
 

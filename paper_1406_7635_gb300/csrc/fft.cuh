@@ -224,23 +224,33 @@ struct FftG<L, DIR, NP, NT, INNER, BS, ES, TWL, IS, P, true> {
                                              int = L, int = L) {}
 };
 
-// The same transform on pencils owned by the calling warp (all 32 lanes call
-// it; only __syncwarp() between passes).
-template <int L, int DIR, int NP, int INNER, int BS, int ES, int TWL = kTwN, int P = 0,
-          bool DONE = (P >= npasses(L))>
-struct FftW;
-template <int L, int DIR, int NP, int INNER, int BS, int ES, int TWL, int P>
-struct FftW<L, DIR, NP, INNER, BS, ES, TWL, P, false> {
-  __device__ __forceinline__ static void run(float2* s, const float2* __restrict__ tw,
-                                             const float2* __restrict__ pre = nullptr) {
-    stockham_pass<L, radix_of(L, P), ns_of(L, P), DIR, NP, 32, INNER, BS, ES, TWL, true>(s, tw,
-                                                                                          P == 0 ? pre : nullptr);
-    FftW<L, DIR, NP, INNER, BS, ES, TWL, P + 1>::run(s, tw);
-  }
+// In-register DFT of length N, natural order in and out: Dft for N <= 16;
+// N = 32 as two 16-point halves (even / odd samples) combined with W_32^k,
+// read from tw32[k] = exp(-2 pi i k / 32) (conjugated for DIR > 0).
+template <int N, int DIR>
+struct RegDft {
+  __device__ __forceinline__ static void run(float2 (&x)[N], const float2* __restrict__) { Dft<N, DIR>::run(x); }
 };
-template <int L, int DIR, int NP, int INNER, int BS, int ES, int TWL, int P>
-struct FftW<L, DIR, NP, INNER, BS, ES, TWL, P, true> {
-  __device__ __forceinline__ static void run(float2*, const float2* __restrict__, const float2* __restrict__ = nullptr) {}
+template <int DIR>
+struct RegDft<32, DIR> {
+  __device__ __forceinline__ static void run(float2 (&x)[32], const float2* __restrict__ tw32) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      e[i] = x[2 * i];
+      o[i] = x[2 * i + 1];
+    }
+    Dft<16, DIR>::run(e);
+    Dft<16, DIR>::run(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float2 w = tw32[k];
+      if (DIR > 0) w.y = -w.y;
+      const float2 t = cmul(o[k], w);
+      x[k] = cadd(e[k], t);
+      x[k + 16] = csub(e[k], t);
+    }
+  }
 };
 
 // pencils stored as rows with pitch PST, twiddles from the global table

@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
                                            const float2* __restrict__ tw, const DevState* __restrict__ st,
                                            BatchArgs ba) {
   // blocks of one cluster share (instance, kx), so these exits are uniform
-  // across the cluster: all its blocks leave together
-  if (st && st->done) return;
+  // across the cluster: all its blocks leave together (the device state's
+  // done flag is read after the predecessor has completed, see below)
   const int inst = blockIdx.x / (g.hx * g.cly * g.clz);
   if (ba.done && ba.done[(long long)inst * ba.done_stride]) return;
   spec += (long long)inst * 3 * g.hx * g.nz * g.ny;
@@ -372,6 +372,13 @@ __global__ void __launch_bounds__(NT, 2) k_yz(Geom g, float2* __restrict__ spec,
   // the spectrum comes from the previous kernel (programmatic dependent
   // launch: wait for it, then let the next kernel's blocks be scheduled)
   grid_dependency_wait();
+  // (a row kernel that gave up a wait sets the done flag while it runs: read
+  // it once the predecessor has completed, so every block sees one value;
+  // the twiddle copies land before the block leaves)
+  if (st && st->done) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
   // 1. load the plane (asynchronous copies, all in flight at once); rows
   //    past the grid are zero; columns y >= ny are never read (the first y
   //    pass is pruned to y < ny)
@@ -483,7 +490,6 @@ template <int LY, int LZ, int NT>
 __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec, const float* __restrict__ kt,
                                             const float2* __restrict__ tw, const DevState* __restrict__ st,
                                             BatchArgs ba) {
-  if (st && st->done) return;   // uniform across the cluster (same instance and kx)
   const int inst = blockIdx.x / (g.hx * g.cly * 2);
   if (ba.done && ba.done[(long long)inst * ba.done_stride]) return;
   spec += (long long)inst * 3 * g.hx * g.nz * g.ny;
@@ -512,6 +518,14 @@ __global__ void __launch_bounds__(NT, 2) k_yz2(Geom g, float2* __restrict__ spec
   const int cstride = g.hx * g.nz * g.ny;
   float2* const plane = spec + kx * g.nz * g.ny;
   grid_dependency_wait();   // the spectrum comes from the previous kernel
+  // the done flag, read once the predecessor has completed: uniform across
+  // the cluster (same instance and kx); the twiddle copies land and the
+  // cluster's arrive is matched before the blocks leave
+  if (st && st->done) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    cluster_wait();
+    return;
+  }
   // 1. load my half of the rows (columns y >= ny are never read: the first
   //    y pass is pruned to y < ny)
   for (int e = threadIdx.x; e < 3 * PH; e += NT) {
@@ -814,6 +828,17 @@ void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, c
 #undef CALL_FX
   // (the y/z and x C2R kernels start while their predecessor drains)
   launch_yz_batch(g, b, s, ba, true);
+#define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
+  MM_ROWL(g.lx, CALL_IX)
+#undef CALL_IX
+}
+
+void launch_demag_fused3(const Geom& g, const Buffers& b, const float* m, float2* T, cudaStream_t s) {
+  const BatchArgs ba{1, nullptr, nullptr, 0};
+#define CALL_FX(LL) run_fx_t<LL>(g, b, m, s, ba)
+  MM_ROWL(g.lx, CALL_FX)
+#undef CALL_FX
+  launch_demag_yz3(g, b, T, s);
 #define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
   MM_ROWL(g.lx, CALL_IX)
 #undef CALL_IX

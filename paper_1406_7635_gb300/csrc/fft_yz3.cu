@@ -1,0 +1,304 @@
+// The (y, z) part of the fused demag convolution (Sec. III.B) for 3-D grids
+// as three kernels over a y-transformed buffer T instead of one cluster per
+// kx plane:
+//
+//   k_yf  y forward: spectrum rows spec[c][kx][z][y] (y < ny, the rest is
+//         zero padding and never read) -> T[kx][c][z][ky], ky < py;
+//   k_zk  one (kx, ky) column of all three components per 6 threads: z
+//         forward (nz inputs, pz points), the kernel product B_i = K_ij M_j
+//         with the octant's mirror signs, z inverse cropped to z < nz, in
+//         place in T;
+//   k_yi  y inverse: T rows -> spectrum rows, cropped to y < ny.
+//
+// Both transforms split their padded length by frequency parity: with
+// k = 2 j + r, the padded DFT restricted to class r is the half-length DFT of
+// x[n] W_P^(r n), exact because the inputs fill at most half the padded
+// length.  The y classes are two pencils per row, transformed by Stockham
+// passes in shared memory; the z classes are held in registers (pz / 2
+// points per thread), one thread per (column, component, class), so the z
+// transforms need no shared-memory passes at all: the threads of a column
+// exchange only the spectra the product needs and, after the inverse, the
+// halves of the two classes (a lane-pair shuffle).
+//
+// Every global access is contiguous: rows of y in and out of the spectrum,
+// rows of ky in T (16-byte pairs (2j, 2j + 1) of the two classes), and in the
+// column kernel runs of consecutive ky for each (component, z).  The kernels
+// are launched with programmatic dependent launch and wait for their
+// predecessor before reading its output; the inverse transforms are
+// unnormalised (the kernel octant carries the 1 / (lx py pz) factor and
+// -mu0).
+#include <algorithm>
+
+#include "fft.cuh"
+#include "mm_internal.h"
+
+namespace mm {
+namespace {
+using namespace mmfft;
+
+constexpr int kYNT = 128;   // threads of the y kernels
+
+// spectrum rows (z) per block of the y kernels: 16 (32 pencils of up to 128
+// points), fewer for longer rows so that a thread holds at most 32 values
+// per pass
+template <int PH>
+struct YCfg {
+  static constexpr int ROWS = PH <= 128 ? 16 : 2048 / PH;
+  static constexpr int NP = 2 * ROWS;         // pencils: class r = p / ROWS, row p % ROWS
+  static constexpr int P = PH + 1;            // pencil pitch (odd: conflict-free columns of pencils)
+  static constexpr size_t SMEM = sizeof(float2) * NP * P;
+};
+
+// y forward of ROWS rows (z0 ..) of one (kx, c) plane
+template <int PH>
+__global__ void __launch_bounds__(kYNT) k_yf(Geom g, const float2* __restrict__ spec, float2* __restrict__ T,
+                                             const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  using Y = YCfg<PH>;
+  constexpr int ROWS = Y::ROWS, P = Y::P;
+  extern __shared__ float2 sm[];
+  __shared__ float2 twh[PH], twc[PH];   // W_PH^i and the class-1 twiddle W_(2 PH)^y
+  const int z0 = blockIdx.x * ROWS, c = blockIdx.y, kx = blockIdx.z;
+  twiddles_async<kYNT>(twh, tw, PH, kTwN / PH);
+  twiddles_async<kYNT>(twc, tw, PH, kTwN / (2 * PH));
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int ny = g.ny, nz = g.nz;
+  // the (c, kx) plane [z][y] of the spectrum (32-bit offsets: 3 hx nz ny < 2^31)
+  const float2* __restrict__ src = spec + (c * g.hx + kx) * nz * ny;
+  grid_dependency_wait();   // the spectrum comes from the previous kernel
+  // (the done flag is read once the predecessor, which may set it, has
+  // completed: every thread sees one value)
+  if (st && st->done) return;
+  for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
+    const int i = e / PH, y = e % PH, z = z0 + i;
+    if (y >= ny) continue;   // zero padding: the first pass reads y < ny only
+    const float2 x = z < nz ? src[z * ny + y] : make_float2(0.f, 0.f);
+    sm[i * P + y] = x;
+    sm[(ROWS + i) * P + y] = cmul(x, twc[y]);
+  }
+  __syncthreads();
+  FftG<PH, -1, Y::NP, kYNT, 1, P, 1, PH>::run(sm, twh, nullptr, ny);
+  // ky = 2 j + r: the two classes' values at j are the pair (2 j, 2 j + 1)
+  float4* __restrict__ dst = reinterpret_cast<float4*>(T) + ((kx * 3 + c) * nz) * PH;
+  for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
+    const int i = e / PH, j = e % PH, z = z0 + i;
+    if (z >= nz) continue;
+    const float2 a = sm[i * P + j], b = sm[(ROWS + i) * P + j];
+    dst[z * PH + j] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// y inverse of ROWS rows of one (kx, c) plane, cropped to y < ny
+template <int PH>
+__global__ void __launch_bounds__(kYNT) k_yi(Geom g, const float2* __restrict__ T, float2* __restrict__ spec,
+                                             const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  using Y = YCfg<PH>;
+  constexpr int ROWS = Y::ROWS, P = Y::P;
+  extern __shared__ float2 sm[];
+  __shared__ float2 twh[PH], twc[PH];
+  const int z0 = blockIdx.x * ROWS, c = blockIdx.y, kx = blockIdx.z;
+  twiddles_async<kYNT>(twh, tw, PH, kTwN / PH);
+  twiddles_async<kYNT>(twc, tw, PH, kTwN / (2 * PH));
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  const int ny = g.ny, nz = g.nz;
+  const float4* __restrict__ src = reinterpret_cast<const float4*>(T) + ((kx * 3 + c) * nz) * PH;
+  grid_dependency_wait();   // T comes from the column kernel
+  if (st && st->done) {      // (after the predecessor: one value for all threads)
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
+  for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
+    const int i = e / PH, j = e % PH, z = z0 + i;
+    const float4 v = z < nz ? src[z * PH + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sm[i * P + j] = make_float2(v.x, v.y);
+    sm[(ROWS + i) * P + j] = make_float2(v.z, v.w);
+  }
+  __syncthreads();
+  FftG<PH, 1, Y::NP, kYNT, 1, P, 1, PH>::run(sm, twh, nullptr, PH, ny);   // outputs y >= ny cropped
+  // x[y] = X_0[y] + conj(W_(2 PH)^y) X_1[y]
+  float2* __restrict__ out = spec + (c * g.hx + kx) * nz * ny;
+  for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
+    const int i = e / PH, y = e % PH, z = z0 + i;
+    if (z >= nz || y >= ny) continue;
+    out[z * ny + y] = cadd(sm[i * P + y], cmul(sm[(ROWS + i) * P + y], cconj(twc[y])));
+  }
+}
+
+constexpr int kZCols = 32;    // (kx, ky) columns per block of the column kernel
+constexpr int kZNT = 192;     // 3 components x 2 classes x 32 columns
+
+template <int LZH>
+struct ZCfg {
+  static constexpr int PZ = 2 * LZH;
+  // pitch (complex values) of one kz row of the block's columns: the two
+  // classes' rows 2 l and 2 l + 1 lie 8 banks of 8 bytes apart, so the 16
+  // lanes of a half-warp (8 columns x 2 classes) hit distinct banks
+  static constexpr int CP = 40;
+  static constexpr size_t SMEM = sizeof(float2) * 3 * PZ * CP;
+};
+
+// Thread (warp w, lane): component c = w % 3, class rz = lane & 1, column
+// 16 (w / 3) + lane / 2 of the block.
+template <int LZH>
+__global__ void __launch_bounds__(kZNT, 3) k_zk(Geom g, float2* __restrict__ T, const float* __restrict__ kt,
+                                             const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  using Z = ZCfg<LZH>;
+  constexpr int PZ = Z::PZ, CP = Z::CP;
+  extern __shared__ float2 sA[];        // [component][kz][column]: the forward spectra
+  __shared__ float2 twz[PZ];            // W_PZ^z
+  __shared__ float2 twl[LZH];           // W_LZH^l (the 32-point register transform)
+  twiddles_async<kZNT>(twz, tw, PZ, kTwN / PZ);
+  twiddles_async<kZNT>(twl, tw, LZH, kTwN / LZH);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp % 3, rz = lane & 1, col = (warp / 3) * 16 + (lane >> 1);
+  const int kx = blockIdx.y, ky = blockIdx.x * kZCols + col;
+  const int nz = g.nz, PY = g.py;
+  // column (kx, c, ., ky) of T, z stride PY (32-bit offsets: 3 hx nz py < 2^31)
+  float2* __restrict__ cp = T + (kx * 3 + c) * nz * PY + ky;
+  grid_dependency_wait();   // T comes from the y kernel
+  if (st && st->done) return;   // (after the predecessor: one value for all threads)
+  // 1. class rz of component c: the LZH-point DFT of a[z] W_PZ^(rz z)
+  float2 v[LZH];
+#pragma unroll
+  for (int z = 0; z < LZH; ++z) v[z] = z < nz ? cp[z * PY] : make_float2(0.f, 0.f);
+  if (rz) {
+#pragma unroll
+    for (int z = 0; z < LZH; ++z) v[z] = cmul(v[z], twz[z]);
+  }
+  RegDft<LZH, -1>::run(v, twl);   // v[l] = A_c(kz = 2 l + rz)
+#pragma unroll
+  for (int l = 0; l < LZH; ++l) sA[(c * PZ + 2 * l + rz) * CP + col] = v[l];
+  __syncthreads();
+  // 2. B_c = sum_j K_cj A_j at kz = 2 l + rz; the octant holds K at (|ky|,
+  //    |kz|) with Kxy odd in y, Kxz odd in z, Kyz odd in both
+  int iy = ky;
+  float sy = 1.f;
+  if (ky > PY / 2) {
+    iy = PY - ky;
+    sy = -1.f;
+  }
+  const int per = g.hky * g.hkz;   // octant: 6 hkx hky hkz < 2^31 floats
+  const float* __restrict__ kp = kt + kx * 6 * per + iy;
+  // tensor components of row c (xx 0, yy 1, zz 2, xy 3, xz 4, yz 5) and which
+  // of them change sign with ky / kz
+  const int t0 = c == 0 ? 0 : (c == 1 ? 3 : 4);
+  const int t1 = c == 0 ? 3 : (c == 1 ? 1 : 5);
+  const int t2 = c == 0 ? 4 : (c == 1 ? 5 : 2);
+  const float fy0 = c == 1 ? sy : 1.f, fy1 = c != 1 ? sy : 1.f, fy2 = c == 1 ? sy : 1.f;
+#pragma unroll
+  for (int l = 0; l < LZH; ++l) {
+    const int kz = 2 * l + rz;
+    int iz = kz;
+    float sz = 1.f;
+    if (kz > PZ / 2) {
+      iz = PZ - kz;
+      sz = -1.f;
+    }
+    const float* __restrict__ q = kp + iz * g.hky;
+    const float k0 = __ldg(q + t0 * per) * fy0 * (c == 2 ? sz : 1.f);
+    const float k1 = __ldg(q + t1 * per) * fy1 * (c == 2 ? sz : 1.f);
+    const float k2 = __ldg(q + t2 * per) * fy2 * (c != 2 ? sz : 1.f);
+    const float2 a0 = sA[kz * CP + col], a1 = sA[(PZ + kz) * CP + col], a2 = sA[(2 * PZ + kz) * CP + col];
+    v[l] = make_float2(fmaf(k2, a2.x, fmaf(k1, a1.x, k0 * a0.x)), fmaf(k2, a2.y, fmaf(k1, a1.y, k0 * a0.y)));
+  }
+  // 3. inverse class transform: v[z] = sum_l B_c(2 l + rz) W_LZH^(-z l)
+  RegDft<LZH, 1>::run(v, twl);
+  // 4. b[z] = V_0[z] + conj(W_PZ^z) V_1[z]: the class-0 lane writes z < LZH / 2,
+  //    the class-1 lane the rest, each with the partner's half by a shuffle
+  constexpr int HH = LZH / 2;
+#pragma unroll
+  for (int i = 0; i < HH; ++i) {
+    const float2 send = rz ? v[i] : v[i + HH];
+    const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1), __shfl_xor_sync(0xffffffffu, send.y, 1));
+    const int z = rz ? i + HH : i;
+    const float2 w = cconj(twz[z]);
+    const float2 b = rz ? cadd(recv, cmul(v[i + HH], w)) : cadd(v[i], cmul(recv, w));
+    if (z < nz) cp[z * PY] = b;
+  }
+}
+
+template <int PH>
+void run_y(const Geom& g, const float2* spec_in, float2* T, float2* spec_out, const float2* tw, const DevState* st,
+           cudaStream_t s, bool forward) {
+  using Y = YCfg<PH>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((g.nz + Y::ROWS - 1) / Y::ROWS, 3, g.hx);
+  cfg.blockDim = dim3(kYNT);
+  cfg.dynamicSmemBytes = Y::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (forward) {
+    cudaFuncSetAttribute(k_yf<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::SMEM);
+    cudaLaunchKernelEx(&cfg, k_yf<PH>, g, spec_in, T, tw, st);
+  } else {
+    cudaFuncSetAttribute(k_yi<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::SMEM);
+    cudaLaunchKernelEx(&cfg, k_yi<PH>, g, (const float2*)T, spec_out, tw, st);
+  }
+}
+
+template <int LZH>
+void run_z(const Geom& g, float2* T, const float* ktf, const float2* tw, const DevState* st, cudaStream_t s) {
+  using Z = ZCfg<LZH>;
+  cudaFuncSetAttribute(k_zk<LZH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::SMEM);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g.py / kZCols, g.hx);
+  cfg.blockDim = dim3(kZNT);
+  cfg.dynamicSmemBytes = Z::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_zk<LZH>, g, T, ktf, tw, st);
+}
+
+void launch_y(const Geom& g, const Buffers& b, float2* T, bool forward, cudaStream_t s) {
+  const float2* in = b.spec;
+  switch (g.py / 2) {
+    case 16: run_y<16>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    case 32: run_y<32>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    case 64: run_y<64>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    case 128: run_y<128>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    case 256: run_y<256>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    case 512: run_y<512>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    default: break;
+  }
+}
+
+}  // namespace
+
+// The three-kernel plan: a fused spectrum layout, open (padded) y and z axes
+// with 32 <= py <= 1024 and 16 <= pz <= 64 (z classes of 8, 16 or 32 points).
+bool yz3_plan(const Geom& g) {
+  return g.fused && g.pbcy == 0 && g.pbcz == 0 && g.py >= 32 && g.py <= 1024 && g.pz >= 16 && g.pz <= 64;
+}
+
+size_t yz3_bytes(const Geom& g) { return sizeof(float2) * (size_t)g.hx * 3 * g.nz * g.py; }
+
+void launch_yz3_part(const Geom& g, const Buffers& b, float2* T, int part, cudaStream_t s) {
+  if (part == 0) {
+    launch_y(g, b, T, true, s);
+  } else if (part == 1) {
+    switch (g.pz / 2) {
+      case 8: run_z<8>(g, T, b.ktf, b.tw, b.st, s); break;
+      case 16: run_z<16>(g, T, b.ktf, b.tw, b.st, s); break;
+      case 32: run_z<32>(g, T, b.ktf, b.tw, b.st, s); break;
+      default: break;
+    }
+  } else {
+    launch_y(g, b, T, false, s);
+  }
+}
+
+void launch_demag_yz3(const Geom& g, const Buffers& b, float2* T, cudaStream_t s) {
+  for (int part = 0; part < 3; ++part) launch_yz3_part(g, b, T, part, s);
+}
+
+}  // namespace mm

@@ -69,6 +69,9 @@ struct mm_ctx {
   int stt_zl = 0, stt_sl = 0;   // switches of mm_enable_stt
   Stt stt{};                     // active spin-transfer torques (set by flush_luts)
   RsMaps maps{};                 // tensor maps of the row-stage kernels (rowstage_maps)
+  int yz_req = 0;                // requested (y, z) kernels: 0 default, 1 cluster, 2 three kernels
+  bool yz3 = false;              // the three-kernel (y, z) path is active
+  float2* yzt = nullptr;         // its y-transformed buffer (yz3_bytes)
   SttLUT* stt_lut = nullptr;     // device table
   int method = 0;                // host copy of DevState::method
   bool lut_dirty = true;
@@ -197,11 +200,50 @@ void invalidate(mm_ctx* c) {
   c->k1_valid = false;
 }
 
+// kernels of the (y, z) part on the fused layout
+int yz_launches(const mm_ctx* c) { return c->yz3 ? 3 : 1; }
+
 // kernels one demag convolution launches (see launch_demag)
-int demag_launches(const Geom& g) {
-  if (g.fused) return 3;
+int demag_launches(const mm_ctx* c) {
+  const Geom& g = c->g;
+  if (g.fused) return 2 + yz_launches(c);
   int mid = g.pz > 1 ? (g.py > 1 ? 3 : 1) : 1;
   return 2 + mid;
+}
+
+// the exact demag convolution of m into nb.bd (nb: the context's buffers,
+// possibly without the device state)
+void demag_exact(mm_ctx* c, const Buffers& nb, const float* m) {
+  if (c->yz3) launch_demag_fused3(c->g, nb, m, c->yzt, c->stream);
+  else launch_demag(c->g, nb, m, c->stream);
+}
+
+// the (y, z) part of the convolution inside the row-stage path
+void demag_yz(mm_ctx* c) {
+  if (c->yz3) launch_demag_yz3(c->g, c->b, c->yzt, c->stream);
+  else launch_demag_yz(c->g, c->b, c->stream);
+}
+
+// Applies the requested (y, z) kernels: the three-kernel path where the grid
+// allows it (default, or asked for), its buffer allocated or freed to match.
+int apply_yz_choice(mm_ctx* c) {
+  const bool want = yz3_plan(c->g) && c->yz_req != 1;
+  if (want && !c->yzt) {
+    cudaError_t e = cudaMalloc((void**)&c->yzt, yz3_bytes(c->g));
+    if (e != cudaSuccess) {
+      c->yzt = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA,
+                  std::string("(y, z) buffer: ") + cudaGetErrorString(e));
+    }
+  }
+  if (!want && c->yzt) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->yzt);
+    c->yzt = nullptr;
+  }
+  if (want != c->yz3) c->graph_valid = false;
+  c->yz3 = want;
+  return MM_OK;
 }
 
 // demag field of the stage input: exact convolution, or the surrogate
@@ -210,7 +252,7 @@ void enqueue_demag(mm_ctx* c) {
   if (c->sur_active)
     launch_fno_demag(c->sur, c->g, c->b, c->b.ms, c->sur_inv_ref, c->sur_mu0_ref, c->b.bd, c->stream);
   else
-    launch_demag(c->g, c->b, c->b.ms, c->stream);
+    demag_exact(c, c->b, c->b.ms);
 }
 
 // The row-stage path (fused convolution layout, exact demag): per attempt one
@@ -225,13 +267,13 @@ bool rowstage_path(const mm_ctx* c) {
 // stage-1 torque at the current m (FSAL start)
 void enqueue_k1(mm_ctx* c) {
   if (rowstage_path(c)) {
-    c->launches += 2 + (c->T.demag ? 1 : 0);
+    c->launches += 2 + (c->T.demag ? yz_launches(c) : 0);
     launch_rowstage(c->g, c->b, c->T, c->maps, 0, 0, 0, c->freq, c->phase, c->stream);
-    if (c->T.demag) launch_demag_yz(c->g, c->b, c->stream);
+    if (c->T.demag) demag_yz(c);
     launch_rowstage(c->g, c->b, c->T, c->maps, 1, 0, 0, c->freq, c->phase, c->stream);
     return;
   }
-  c->launches += 2 + (c->T.demag ? demag_launches(c->g) : 0);
+  c->launches += 2 + (c->T.demag ? demag_launches(c) : 0);
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
   enqueue_demag(c);
   launch_torque_t(c->g, c->b, c->T, c->stt, 0, c->freq, c->phase, c->stream);
@@ -241,7 +283,7 @@ void enqueue_attempt(mm_ctx* c) {
   if (rowstage_path(c)) {
     launch_rowstage(c->g, c->b, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
     for (int s = 1; s < 7; ++s) {
-      if (c->T.demag) launch_demag_yz(c->g, c->b, c->stream);
+      if (c->T.demag) demag_yz(c);
       launch_rowstage(c->g, c->b, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
     }
     return;
@@ -334,7 +376,7 @@ int eval_field(mm_ctx* c, int mode) {
   Buffers nb = c->b;
   nb.st = nullptr;    // getters ignore the stepping loop's done flag
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
-  if (c->T.demag || mode == 3) launch_demag(c->g, nb, c->b.ms, c->stream);
+  if (c->T.demag || mode == 3) demag_exact(c, nb, c->b.ms);
   if (mode == 3) return MM_OK;
   if (mode == 2 || mode == 4) MM_CUDA(cudaMemsetAsync(c->b.acc, 0, 9 * sizeof(double), c->stream));
   Terms T = c->T;
@@ -487,10 +529,12 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   if (rc) return cleanup(rc);
   rc = flush_luts(c);
   if (rc) return cleanup(rc);
+  rc = apply_yz_choice(c);
+  if (rc) return cleanup(rc);
   // one convolution outside any capture: sets per-kernel launch attributes
   Buffers nb = b;
   nb.st = nullptr;
-  launch_demag(g, nb, b.ms, c->stream);
+  demag_exact(c, nb, b.ms);
   e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && g.fused) e = prepare_rowstage(g);
@@ -508,7 +552,7 @@ int mm_destroy(mm_ctx* c) {
   Buffers& b = c->b;
   void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.ms2, b.bd, b.out,
                   b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.code, b.st, b.hist, b.acc,
-                  b.fixed, c->sur_acc, c->stt_lut};
+                  b.fixed, c->sur_acc, c->stt_lut, c->yzt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -720,7 +764,7 @@ static int surrogate_check(mm_ctx* c) {
   Buffers nb = c->b;
   nb.st = nullptr;
   launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
-  launch_demag(c->g, nb, c->b.ms, c->stream);                     // exact -> bd
+  demag_exact(c, nb, c->b.ms);                                     // exact -> bd
   launch_fno_demag(c->sur, c->g, c->b, c->b.ms, c->sur_inv_ref, c->sur_mu0_ref, c->b.out, c->stream);
   launch_rel_err(3 * c->g.n, c->b.out, c->b.bd, c->sur_acc, c->stream);
   double acc[2];
@@ -873,10 +917,18 @@ int mm_set_pbc(mm_ctx* c, int px, int py, int pz) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   c->g = g;
   if (e == cudaSuccess) {
+    // the (y, z) buffer's size follows the transform lengths
+    if (c->yzt) {
+      cudaFree(c->yzt);
+      c->yzt = nullptr;
+    }
+    c->yz3 = false;
+    const int rc = apply_yz_choice(c);
+    if (rc) return rc;
     // one convolution outside any capture (launch attributes), as at creation
     Buffers nb = b;
     nb.st = nullptr;
-    launch_demag(g, nb, b.ms, c->stream);
+    demag_exact(c, nb, b.ms);
     e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
   }
@@ -1141,7 +1193,7 @@ int mm_demag_apply(mm_ctx* c, const float* m, float* b) {
   Buffers nb = c->b;
   nb.st = nullptr;
   nb.bd = b;
-  launch_demag(c->g, nb, m, c->stream);
+  demag_exact(c, nb, m);
   MM_CUDA(cudaGetLastError());
   MM_CUDA(cudaStreamSynchronize(c->stream));
   return MM_OK;
@@ -1258,7 +1310,7 @@ int mm_surrogate_train(mm_ctx* c, mm_fno* net, double ms_ref, int n_pairs, int t
     // pair: u = Msat m / ms_ref, y = B_demag / (mu0 ms_ref), exact convolution
     launch_copy_mcur(c->g, c->b, c->b.ms, c->stream);
     launch_to_u(c->g, c->b, c->b.ms, inv_ref, U + (size_t)p * n3, c->stream);
-    launch_demag(c->g, nb, c->b.ms, c->stream);
+    demag_exact(c, nb, c->b.ms);
     launch_scale(n3, c->b.bd, inv_mu, Y + (size_t)p * n3, c->stream);
   }
   MM_CUDA(cudaStreamSynchronize(c->stream));
@@ -1311,6 +1363,27 @@ int mm_sync(mm_ctx* c) {
   return MM_OK;
 }
 
+int mm_set_yz_kernels(mm_ctx* c, int which, int* active) {
+  if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
+  if (which < 0 || which > 2) return fail(MM_ERR_ARG, "which must be 0 (default), 1 (cluster) or 2 (three kernels)");
+  if (which == 2 && !yz3_plan(c->g))
+    return fail(MM_ERR_ARG, "the three-kernel (y, z) path needs open y and z axes, py >= 32 and 16 <= pz <= 64");
+  MM_CUDA(cudaStreamSynchronize(c->stream));
+  c->yz_req = which;
+  const int rc = apply_yz_choice(c);
+  if (rc) return rc;
+  if (c->yz3) {
+    // one convolution outside any capture (launch attributes)
+    Buffers nb = c->b;
+    nb.st = nullptr;
+    demag_exact(c, nb, c->b.ms);
+    MM_CUDA(cudaStreamSynchronize(c->stream));
+    MM_CUDA(cudaGetLastError());
+  }
+  if (active) *active = c->g.fused ? (c->yz3 ? 2 : 1) : 0;
+  return MM_OK;
+}
+
 int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us, int* n_out) {
   if (!c || attempts < 1 || max < 1 || !kinds || !us || !n_out) return fail(MM_ERR_ARG, "bad profiling arguments");
   if (!c->m_set) return fail(MM_ERR_STATE, "m has not been set");
@@ -1318,11 +1391,19 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
   int rc = flush_luts(c);
   if (rc) return rc;
   // launch positions of one attempt: the prep kernel, then per stage the
-  // (y, z) kernel (with demag) and the row kernel
+  // (y, z) kernel(s) (with demag) and the row kernel
   std::vector<int> kind;
   kind.push_back(0);
   for (int s = 1; s < 7; ++s) {
-    if (c->T.demag) kind.push_back(1);
+    if (c->T.demag) {
+      if (c->yz3) {
+        kind.push_back(3);
+        kind.push_back(4);
+        kind.push_back(5);
+      } else {
+        kind.push_back(1);
+      }
+    }
     kind.push_back(2);
   }
   const int P = (int)kind.size();
@@ -1349,7 +1430,15 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
     launch_rowstage(c->g, c->b, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
     e = cudaEventRecord(ev[q++], c->stream);
     for (int s = 1; s < 7 && e == cudaSuccess; ++s) {
-      if (c->T.demag) {
+      if (c->T.demag && c->yz3) {
+        // the three kernels of launch_demag_yz3, one event after each
+        launch_yz3_part(c->g, c->b, c->yzt, 0, c->stream);
+        e = cudaEventRecord(ev[q++], c->stream);
+        launch_yz3_part(c->g, c->b, c->yzt, 1, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[q++], c->stream);
+        launch_yz3_part(c->g, c->b, c->yzt, 2, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[q++], c->stream);
+      } else if (c->T.demag) {
         launch_demag_yz(c->g, c->b, c->stream);
         e = cudaEventRecord(ev[q++], c->stream);
       }

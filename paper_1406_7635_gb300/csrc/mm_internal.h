@@ -184,6 +184,17 @@ void launch_demag_fused_batch(const Geom& g, const Buffers& b, const float* m, c
 void launch_kt_transpose(const Geom& g, const float* kt, float* ktf, cudaStream_t s);
 // only the (y, z) part of the fused convolution (k_yz), spectrum in place
 void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s);
+// The three-kernel (y, z) part (fft_yz3.cu): y forward into T (yz3_bytes(g)
+// bytes, [kx][c][z][ky]), the column kernel (z, kernel product, z inverse)
+// in place in T, y inverse back into the spectrum; yz3_plan(g) tells whether
+// the grid supports it.  launch_demag_fused3: the whole convolution with it.
+bool yz3_plan(const Geom& g);
+size_t yz3_bytes(const Geom& g);
+void launch_demag_yz3(const Geom& g, const Buffers& b, float2* T, cudaStream_t s);
+void launch_demag_fused3(const Geom& g, const Buffers& b, const float* m, float2* T, cudaStream_t s);
+// one of the three kernels of launch_demag_yz3 (0 y forward, 1 column
+// kernel, 2 y inverse), for per-kernel timing
+void launch_yz3_part(const Geom& g, const Buffers& b, float2* T, int part, cudaStream_t s);
 // Tensor maps of the row-stage kernels' TMA path (rowstage.cu): the spectrum
 // [3][hx][nz][ny] (8-byte elements) with box (ROWS, 1, L + 1, 3), the stage
 // inputs [3][nz][ny][nx] with boxes (L, ROWS + 2, 1, 1) (own plane and the

@@ -324,7 +324,13 @@ template <int L, int ROWS, int NT, bool SL, bool SS, bool TT>
 __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Ptrs p, DevState* __restrict__ st,
                                                  StageCoef* __restrict__ sc, int s, int mode, double freq,
                                                  double phase_over_pi, const __grid_constant__ RsMaps maps) {
-  if (st->done) return;   // uniform: the controller runs after every block of this launch
+  // The done flag is read once per block: the controller runs after every
+  // block of this launch, but a block that gave up a wait on its copies sets
+  // the flag while others may be starting, and the block must agree.
+  __shared__ int blk_done;
+  if (threadIdx.x == 0) blk_done = st->done;
+  __syncthreads();
+  if (blk_done) return;
   using SM = RsSmem<L, ROWS>;
   constexpr int PST = SM::PST, NR = SM::NR;
   // real cells per thread: ROWS rows of at most L cells (nx <= 2L, and the

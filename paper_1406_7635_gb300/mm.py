@@ -105,6 +105,7 @@ _SIGS = {
     "mm_demag_field_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _P, _P, _P]),
     "mm_sync": (_I, [_P]),
     "mm_profile_attempts": (_I, [_P, _I, _I, _P, _P, C.POINTER(_I)]),
+    "mm_set_yz_kernels": (_I, [_P, _I, C.POINTER(_I)]),
     "mm_fp32_peak": (_I, [_I, _I, C.POINTER(_D), C.POINTER(_I), C.POINTER(_I)]),
     "mm_batch_create": (_I, [C.POINTER(_P), _I, C.POINTER(mm_instance_spec), _I, _P]),
     "mm_batch_destroy": (_I, [_P]),
@@ -172,7 +173,7 @@ def fp32_peak(device=0, reps=5):
     return tf.value, sms.value, mhz.value
 
 
-KERNEL_KINDS = {0: "prep", 1: "yz", 2: "row"}
+KERNEL_KINDS = {0: "prep", 1: "yz", 2: "row", 3: "yf", 4: "zk", 5: "yi"}
 
 
 class Context:
@@ -357,6 +358,13 @@ class Context:
 
     def sync(self):
         _check(mm_sync(self.h))
+
+    def set_yz_kernels(self, which):
+        """(y, z) kernels of the convolution: 0 default, 1 cluster kernel, 2
+        three kernels; returns the kernels in use (mm_set_yz_kernels)."""
+        a = C.c_int()
+        _check(mm_set_yz_kernels(self.h, int(which), C.byref(a)))
+        return a.value
 
     def profile_attempts(self, attempts):
         """Per launch position of one RK45 attempt: (kind, mean microseconds)
