@@ -36,22 +36,28 @@ namespace mm {
 namespace {
 using namespace mmfft;
 
-constexpr int kYNT = 128;   // threads of the y kernels
+// Threads of the y kernels.  Small blocks (two warps, 8 rows of up to 128
+// points) keep every block of the 128 x 128 x 32 grid (4 z chunks x 3
+// components x 129 kx planes) resident at once: 12 blocks per SM.
+constexpr int kYNT = 64;
+constexpr int y_min_blocks(int PH) { return PH >= 512 ? 8 : 12; }   // (rows of 512: more registers)
 
-// spectrum rows (z) per block of the y kernels: 16 (32 pencils of up to 128
+// spectrum rows (z) per block of the y kernels: 8 (16 pencils of up to 128
 // points), fewer for longer rows so that a thread holds at most 32 values
 // per pass
 template <int PH>
 struct YCfg {
-  static constexpr int ROWS = PH <= 128 ? 16 : 2048 / PH;
+  static constexpr int ROWS = PH <= 128 ? 8 : 1024 / PH;
   static constexpr int NP = 2 * ROWS;         // pencils: class r = p / ROWS, row p % ROWS
   static constexpr int P = PH + 1;            // pencil pitch (odd: conflict-free columns of pencils)
   static constexpr size_t SMEM = sizeof(float2) * NP * P;
 };
 
-// y forward of ROWS rows (z0 ..) of one (kx, c) plane
+// y forward of ROWS rows (z0 ..) of one (kx, c) plane.  The rows land in
+// the class-0 pencils by asynchronous copies (all in flight at once); the
+// class-1 pencils are x W_(2 PH)^y of them.
 template <int PH>
-__global__ void __launch_bounds__(kYNT) k_yf(Geom g, const float2* __restrict__ spec, float2* __restrict__ T,
+__global__ void __launch_bounds__(kYNT, y_min_blocks(PH)) k_yf(Geom g, const float2* __restrict__ spec, float2* __restrict__ T,
                                              const float2* __restrict__ tw, const DevState* __restrict__ st) {
   using Y = YCfg<PH>;
   constexpr int ROWS = Y::ROWS, P = Y::P;
@@ -60,21 +66,27 @@ __global__ void __launch_bounds__(kYNT) k_yf(Geom g, const float2* __restrict__ 
   const int z0 = blockIdx.x * ROWS, c = blockIdx.y, kx = blockIdx.z;
   twiddles_async<kYNT>(twh, tw, PH, kTwN / PH);
   twiddles_async<kYNT>(twc, tw, PH, kTwN / (2 * PH));
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
   const int ny = g.ny, nz = g.nz;
   // the (c, kx) plane [z][y] of the spectrum (32-bit offsets: 3 hx nz ny < 2^31)
   const float2* __restrict__ src = spec + (c * g.hx + kx) * nz * ny;
   grid_dependency_wait();   // the spectrum comes from the previous kernel
   // (the done flag is read once the predecessor, which may set it, has
   // completed: every thread sees one value)
-  if (st && st->done) return;
+  if (st && st->done) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
   for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
     const int i = e / PH, y = e % PH, z = z0 + i;
     if (y >= ny) continue;   // zero padding: the first pass reads y < ny only
-    const float2 x = z < nz ? src[z * ny + y] : make_float2(0.f, 0.f);
-    sm[i * P + y] = x;
-    sm[(ROWS + i) * P + y] = cmul(x, twc[y]);
+    if (z < nz) cp_async_f2(&sm[i * P + y], src + z * ny + y);
+    else sm[i * P + y] = make_float2(0.f, 0.f);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
+    const int i = e / PH, y = e % PH;
+    if (y < ny) sm[(ROWS + i) * P + y] = cmul(sm[i * P + y], twc[y]);
   }
   __syncthreads();
   FftG<PH, -1, Y::NP, kYNT, 1, P, 1, PH>::run(sm, twh, nullptr, ny);
@@ -88,9 +100,10 @@ __global__ void __launch_bounds__(kYNT) k_yf(Geom g, const float2* __restrict__ 
   }
 }
 
-// y inverse of ROWS rows of one (kx, c) plane, cropped to y < ny
+// y inverse of ROWS rows of one (kx, c) plane, cropped to y < ny; the T rows
+// land de-interleaved in the two class pencils by asynchronous copies
 template <int PH>
-__global__ void __launch_bounds__(kYNT) k_yi(Geom g, const float2* __restrict__ T, float2* __restrict__ spec,
+__global__ void __launch_bounds__(kYNT, y_min_blocks(PH)) k_yi(Geom g, const float2* __restrict__ T, float2* __restrict__ spec,
                                              const float2* __restrict__ tw, const DevState* __restrict__ st) {
   using Y = YCfg<PH>;
   constexpr int ROWS = Y::ROWS, P = Y::P;
@@ -99,9 +112,8 @@ __global__ void __launch_bounds__(kYNT) k_yi(Geom g, const float2* __restrict__ 
   const int z0 = blockIdx.x * ROWS, c = blockIdx.y, kx = blockIdx.z;
   twiddles_async<kYNT>(twh, tw, PH, kTwN / PH);
   twiddles_async<kYNT>(twc, tw, PH, kTwN / (2 * PH));
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
   const int ny = g.ny, nz = g.nz;
-  const float4* __restrict__ src = reinterpret_cast<const float4*>(T) + ((kx * 3 + c) * nz) * PH;
+  const float2* __restrict__ src = T + ((kx * 3 + c) * nz) * (2 * PH);
   grid_dependency_wait();   // T comes from the column kernel
   if (st && st->done) {      // (after the predecessor: one value for all threads)
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -109,10 +121,14 @@ __global__ void __launch_bounds__(kYNT) k_yi(Geom g, const float2* __restrict__ 
   }
   for (int e = threadIdx.x; e < ROWS * PH; e += kYNT) {
     const int i = e / PH, j = e % PH, z = z0 + i;
-    const float4 v = z < nz ? src[z * PH + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-    sm[i * P + j] = make_float2(v.x, v.y);
-    sm[(ROWS + i) * P + j] = make_float2(v.z, v.w);
+    if (z < nz) {
+      cp_async_f2(&sm[i * P + j], src + z * (2 * PH) + 2 * j);
+      cp_async_f2(&sm[(ROWS + i) * P + j], src + z * (2 * PH) + 2 * j + 1);
+    } else {
+      sm[i * P + j] = sm[(ROWS + i) * P + j] = make_float2(0.f, 0.f);
+    }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   FftG<PH, 1, Y::NP, kYNT, 1, P, 1, PH>::run(sm, twh, nullptr, PH, ny);   // outputs y >= ny cropped
   // x[y] = X_0[y] + conj(W_(2 PH)^y) X_1[y]
@@ -124,23 +140,26 @@ __global__ void __launch_bounds__(kYNT) k_yi(Geom g, const float2* __restrict__ 
   }
 }
 
-constexpr int kZCols = 32;    // (kx, ky) columns per block of the column kernel
-constexpr int kZNT = 192;     // 3 components x 2 classes x 32 columns
+// (kx, ky) columns per block of the column kernel and its threads: 3
+// components x 2 classes x 16 columns.  Blocks of three warps (25 KB of
+// shared memory at pz = 64) leave 7 per SM resident; the 128 x 128 x 32 grid
+// has 16 x 129 of them, just under two rounds.
+constexpr int kZCols = 16;
+constexpr int kZNT = 96;
+constexpr int kZMinBlocks = 7;
 
 template <int LZH>
 struct ZCfg {
   static constexpr int PZ = 2 * LZH;
-  // pitch (complex values) of one kz row of the block's columns: the two
-  // classes' rows 2 l and 2 l + 1 lie 8 banks of 8 bytes apart, so the 16
-  // lanes of a half-warp (8 columns x 2 classes) hit distinct banks
-  static constexpr int CP = 40;
+  static constexpr int CP = kZCols;   // complex values per kz row of the block's columns
   static constexpr size_t SMEM = sizeof(float2) * 3 * PZ * CP;
 };
 
-// Thread (warp w, lane): component c = w % 3, class rz = lane & 1, column
-// 16 (w / 3) + lane / 2 of the block.
+// Thread (warp w, lane): component c = w, class rz = lane / 16, column
+// lane % 16 of the block (a half-warp holds 16 consecutive columns of one
+// class: conflict-free rows of the shared spectra).
 template <int LZH>
-__global__ void __launch_bounds__(kZNT, 3) k_zk(Geom g, float2* __restrict__ T, const float* __restrict__ kt,
+__global__ void __launch_bounds__(kZNT, kZMinBlocks) k_zk(Geom g, float2* __restrict__ T, const float* __restrict__ kt,
                                              const float2* __restrict__ tw, const DevState* __restrict__ st) {
   using Z = ZCfg<LZH>;
   constexpr int PZ = Z::PZ, CP = Z::CP;
@@ -151,8 +170,8 @@ __global__ void __launch_bounds__(kZNT, 3) k_zk(Geom g, float2* __restrict__ T, 
   twiddles_async<kZNT>(twl, tw, LZH, kTwN / LZH);
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = warp % 3, rz = lane & 1, col = (warp / 3) * 16 + (lane >> 1);
+  const int lane = threadIdx.x & 31;
+  const int c = threadIdx.x >> 5, rz = lane >> 4, col = lane & 15;
   const int kx = blockIdx.y, ky = blockIdx.x * kZCols + col;
   const int nz = g.nz, PY = g.py;
   // column (kx, c, ., ky) of T, z stride PY (32-bit offsets: 3 hx nz py < 2^31)
@@ -171,47 +190,75 @@ __global__ void __launch_bounds__(kZNT, 3) k_zk(Geom g, float2* __restrict__ T, 
 #pragma unroll
   for (int l = 0; l < LZH; ++l) sA[(c * PZ + 2 * l + rz) * CP + col] = v[l];
   __syncthreads();
-  // 2. B_c = sum_j K_cj A_j at kz = 2 l + rz; the octant holds K at (|ky|,
-  //    |kz|) with Kxy odd in y, Kxz odd in z, Kyz odd in both
-  int iy = ky;
-  float sy = 1.f;
-  if (ky > PY / 2) {
-    iy = PY - ky;
-    sy = -1.f;
-  }
-  const int per = g.hky * g.hkz;   // octant: 6 hkx hky hkz < 2^31 floats
-  const float* __restrict__ kp = kt + kx * 6 * per + iy;
-  // tensor components of row c (xx 0, yy 1, zz 2, xy 3, xz 4, yz 5) and which
-  // of them change sign with ky / kz
-  const int t0 = c == 0 ? 0 : (c == 1 ? 3 : 4);
-  const int t1 = c == 0 ? 3 : (c == 1 ? 1 : 5);
-  const int t2 = c == 0 ? 4 : (c == 1 ? 5 : 2);
-  const float fy0 = c == 1 ? sy : 1.f, fy1 = c != 1 ? sy : 1.f, fy2 = c == 1 ? sy : 1.f;
+  // 2. the kernel product B_i = sum_j K_ij A_j at every (kz, column) point of
+  //    the block, all three components per point, in place in sA; point q:
+  //    column q % 32, kz = q / 32 (consecutive lanes on consecutive columns:
+  //    conflict-free shared memory, coalesced octant rows).  The octant holds
+  //    K at (|ky|, |kz|): Kxy is odd in ky, Kxz in kz, Kyz in both.
+  {
+    constexpr int NPTS = PZ * kZCols;
+    constexpr int NPT = (NPTS + kZNT - 1) / kZNT;   // points per thread
+    constexpr int CH = 4;                           // points whose loads are issued together
+    const int per = g.hky * g.hkz;                  // octant: 6 hkx hky hkz < 2^31 floats
+    const float* __restrict__ kpx = kt + kx * 6 * per;
 #pragma unroll
-  for (int l = 0; l < LZH; ++l) {
-    const int kz = 2 * l + rz;
-    int iz = kz;
-    float sz = 1.f;
-    if (kz > PZ / 2) {
-      iz = PZ - kz;
-      sz = -1.f;
+    for (int k0 = 0; k0 < NPT; k0 += CH) {
+      float kc[CH][6];
+      float2 A[CH][3];
+      float sgy[CH], sgz[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int q = threadIdx.x + (k0 + u) * kZNT;
+        if (k0 + u >= NPT || (NPTS % kZNT != 0 && q >= NPTS)) continue;
+        const int pc = q % kZCols, kz = q / kZCols;
+        const int pky = blockIdx.x * kZCols + pc;
+        int iy = pky, iz = kz;
+        sgy[u] = 1.f;
+        sgz[u] = 1.f;
+        if (pky > PY / 2) {
+          iy = PY - pky;
+          sgy[u] = -1.f;
+        }
+        if (kz > PZ / 2) {
+          iz = PZ - kz;
+          sgz[u] = -1.f;
+        }
+        const float* __restrict__ kq = kpx + iz * g.hky + iy;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) kc[u][t] = __ldg(kq + t * per);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[u][j] = sA[(j * PZ + kz) * CP + pc];
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int q = threadIdx.x + (k0 + u) * kZNT;
+        if (k0 + u >= NPT || (NPTS % kZNT != 0 && q >= NPTS)) continue;
+        const int pc = q % kZCols, kz = q / kZCols;
+        const float kxx = kc[u][0], kyy = kc[u][1], kzz = kc[u][2];
+        const float kxy = sgy[u] * kc[u][3], kxz = sgz[u] * kc[u][4], kyz = sgy[u] * sgz[u] * kc[u][5];
+        const float2 X = A[u][0], Y = A[u][1], Zc = A[u][2];
+        sA[kz * CP + pc] = make_float2(kxx * X.x + kxy * Y.x + kxz * Zc.x, kxx * X.y + kxy * Y.y + kxz * Zc.y);
+        sA[(PZ + kz) * CP + pc] =
+            make_float2(kxy * X.x + kyy * Y.x + kyz * Zc.x, kxy * X.y + kyy * Y.y + kyz * Zc.y);
+        sA[(2 * PZ + kz) * CP + pc] =
+            make_float2(kxz * X.x + kyz * Y.x + kzz * Zc.x, kxz * X.y + kyz * Y.y + kzz * Zc.y);
+      }
     }
-    const float* __restrict__ q = kp + iz * g.hky;
-    const float k0 = __ldg(q + t0 * per) * fy0 * (c == 2 ? sz : 1.f);
-    const float k1 = __ldg(q + t1 * per) * fy1 * (c == 2 ? sz : 1.f);
-    const float k2 = __ldg(q + t2 * per) * fy2 * (c != 2 ? sz : 1.f);
-    const float2 a0 = sA[kz * CP + col], a1 = sA[(PZ + kz) * CP + col], a2 = sA[(2 * PZ + kz) * CP + col];
-    v[l] = make_float2(fmaf(k2, a2.x, fmaf(k1, a1.x, k0 * a0.x)), fmaf(k2, a2.y, fmaf(k1, a1.y, k0 * a0.y)));
   }
+  __syncthreads();
+#pragma unroll
+  for (int l = 0; l < LZH; ++l) v[l] = sA[(c * PZ + 2 * l + rz) * CP + col];
   // 3. inverse class transform: v[z] = sum_l B_c(2 l + rz) W_LZH^(-z l)
   RegDft<LZH, 1>::run(v, twl);
   // 4. b[z] = V_0[z] + conj(W_PZ^z) V_1[z]: the class-0 lane writes z < LZH / 2,
-  //    the class-1 lane the rest, each with the partner's half by a shuffle
+  //    the class-1 lane (16 lanes up) the rest, each with the partner's half
+  //    by a shuffle
   constexpr int HH = LZH / 2;
 #pragma unroll
   for (int i = 0; i < HH; ++i) {
     const float2 send = rz ? v[i] : v[i + HH];
-    const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1), __shfl_xor_sync(0xffffffffu, send.y, 1));
+    const float2 recv =
+        make_float2(__shfl_xor_sync(0xffffffffu, send.x, 16), __shfl_xor_sync(0xffffffffu, send.y, 16));
     const int z = rz ? i + HH : i;
     const float2 w = cconj(twz[z]);
     const float2 b = rz ? cadd(recv, cmul(v[i + HH], w)) : cadd(v[i], cmul(recv, w));

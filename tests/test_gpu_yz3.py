@@ -112,10 +112,9 @@ def test_switching_paths_between_steps_keeps_the_trajectory(mm):
     p = grid_problem((12, 47, 40), seed=11)
     a = mm.Context.from_problem(p)
     a.set_yz_kernels(1)
-    a.set_fixed_dt_sequence(np.full(8, 2e-13))
-    a.step(8)
+    a.step(8)                      # adaptive; b replays the same step sizes
     b = mm.Context.from_problem(p)
-    b.set_fixed_dt_sequence(np.full(8, 2e-13))
+    b.set_fixed_dt_sequence(a.get_dt_history())
     b.set_yz_kernels(2)
     b.step(4)
     b.set_yz_kernels(1)
