@@ -204,6 +204,21 @@ def yz_kernel_bytes(p):
     return fused, floor
 
 
+def row_kernel_bytes(p):
+    """Algorithmic HBM bytes of one row-stage kernel launch, the mean over the
+    six launches of an attempt: read the demag spectrum rows and the stage
+    input (its stencil neighbours are the same array) and the cell codes,
+    read m and the earlier stages' k the Dormand-Prince rows need (2, 3, 4,
+    5, 5 arrays for stages 2..6 with m; 5 k's for the error of the last),
+    write k_s, and the next stage input and its spectrum rows (stages 2..6)
+    or the candidate m (the last): 69 MB at 128 x 128 x 32."""
+    arr = 12 * p.ncells                      # one float32 3-vector field
+    spec = _spectrum_rows_bytes(p)
+    earlier = [2, 3, 4, 5, 5, 5]             # arrays read per launch (m + k's; the last: 5 k's)
+    per = [spec + arr + 4 * p.ncells + e * arr + arr + (arr + spec if i < 5 else arr) for i, e in enumerate(earlier)]
+    return sum(per) / len(per)
+
+
 def algorithmic_demag_flops(p):
     """Floating-point operations of one demag convolution, counted as 5 L
     log2 L per complex transform of length L and 2.5 L log2 L per real one,
@@ -461,6 +476,14 @@ def run_ours(args, rank, world, local_rank):
                     "peak_kind": f"measured FP32 FMA throughput (mm_fp32_peak, {sms} SMs, max {sm_clock} MHz)",
                     "frac": round(yz_flops / t_yz / 1e12 / fp32_tflops, 4)},
         }
+    roofline_row = None
+    if "row" in per_kind:
+        t_row = per_kind["row"]["mean_us"] * 1e-6
+        rb = row_kernel_bytes(p)
+        roofline_row = {"bound": "hbm", "achieved": round(rb / t_row / 1e9, 1), "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": round(rb / t_row / 1e9 / peaks["hbm_gbs"], 4),
+                        "kernel": "row-stage kernel k_rs_row (x C2R, field, torque, stage update, x R2C)",
+                        "algorithmic_bytes": rb, "avg_launch_us": round(t_row * 1e6, 2)}
     step_kernels = {"per_kind": per_kind,
                     "sum_us_per_attempt": round(sum(us for _, us in prof), 1),
                     "graph_us_per_attempt": round(t_max / max(attempts, 1) * 1e6, 1),
@@ -519,10 +542,15 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed before every timed step (256 MB write)",
                    "evals_per_step": evals_per_step, "rejected_attempts": int(s1["rejected"] - s0["rejected"])},
         "cell_evals_per_s": value * evals_per_step,
-        "roofline": roofline, "step_kernels": step_kernels, "convolution": convolution,
+        "roofline": roofline, "roofline_row": roofline_row, "step_kernels": step_kernels,
+        "convolution": convolution,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
     }
 
+    # (side lines and the surrogate describe one GPU: measured at N = 1 only;
+    # the batch is sharded over the ranks)
+    if world > 1:
+        args.side = args.surrogate = False
     if args.side and args.workload != SIDE_WORKLOAD:
         ps = WORKLOADS[SIDE_WORKLOAD]()
         cs, ds, _, _, _ = timed_steps(ps, K, W)
@@ -546,7 +574,7 @@ def run_ours(args, rank, world, local_rank):
         cf.close()
         out["general_path"] = general
     if args.batch:
-        out["batch"] = run_batch(args, local_rank)
+        out["batch"] = run_batch(args, local_rank, rank, world)
     if args.surrogate:
         out["surrogate"] = run_surrogate(args, local_rank)
     return out
@@ -563,55 +591,81 @@ def _replay_instance(spec, m0, dts, m_gpu):
     return float(np.abs(m_gpu.astype(np.float64) - ora.m).max())
 
 
-def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2, acc_per_shape=8, t_acc=5e-12):
+def run_batch(args, local_rank, rank=0, world=1, t_end=0.1e-9, seq_per_shape=2, acc_per_shape=8,
+              t_acc=(2e-12, 5e-12)):
     """The batched form: 512 independent instances of four grid sizes, each
     with its own adaptive step, advanced to t_end by one graph launch; against
     the plain single-instance path run one instance after another on a
     stratified sample (seq_per_shape instances of each grid size),
-    extrapolated by the number of instances of each size.  Accuracy: the same
-    batch restarted and run to t_acc, acc_per_shape instances of each size
-    replayed by the float64 oracle with their own step sizes."""
+    extrapolated by the number of instances of each size.  Accuracy: a batch
+    of acc_per_shape instances of each size run to each horizon of t_acc,
+    replayed by the float64 oracle with their own step sizes.  With several ranks the 512
+    instances are sharded round-robin (one batch per GPU, no collective while
+    they run) and the per-instance stats all-gathered at the end; the
+    sequential sample and the accuracy leg run on rank 0."""
     import multiprocessing as mp
     import torch
     from paper_1406_7635_gb300 import mm
+    from paper_1406_7635_gb300.shard import gather_instance_stats, instance_shard
     from paper_1406_7635_gb300.workloads import batch_instances, problem_from_instance
     specs, m0s = batch_instances(512)
-    b = mm.Batch(specs, device=local_rank)
+    ids = instance_shard(len(specs), rank, world)
+    b = mm.Batch([specs[i] for i in ids], device=local_rank)
     tiles = [b.class_info(c) for c in range(b.num_classes())]
-    for i, m in enumerate(m0s):
-        b.set_m(i, m)
+    for j, i in enumerate(ids):
+        b.set_m(j, m0s[i])
     b.run(1e-15)                      # warm-up: builds and instantiates the graph
-    for i, m in enumerate(m0s):
-        b.set_m(i, m)
+    for j, i in enumerate(ids):
+        b.set_m(j, m0s[i])
     b.set_solver()                    # restart the step-size controller
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.run(t_end + 1e-15)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    stats = [b.get_stats(i) for i in range(len(specs))]
+    wall = max_over_ranks(time.perf_counter() - t0, world, torch.device("cuda", local_rank))
+    local_stats = [b.get_stats(j) for j in range(len(ids))]
+    stats = gather_instance_stats(ids, local_stats, len(specs), world, device=f"cuda:{local_rank}")
     cell_steps = sum(s["accepted"] * sp["nx"] * sp["ny"] * sp["nz"] for s, sp in zip(stats, specs))
     shapes = {}
     for i, sp in enumerate(specs):
         shapes.setdefault((sp["nx"], sp["ny"], sp["nz"]), []).append(i)
     b.close()
+    base = {"workload": "batch512 (32x32x1, 64x32x1, 128x64x2, 96x96x4; 4 nm cells)", "instances": len(specs),
+            "t_end_s": t_end, "wall_s": wall, "instances_per_s": len(specs) / wall,
+            "cell_steps_per_s": cell_steps / wall,
+            "accepted_steps_mean": float(np.mean([s["accepted"] for s in stats])),
+            "sharding": f"{world} rank(s), round-robin by instance, stats all-gathered at the end",
+            "autotuned_tiles": tiles}
+    if rank != 0:
+        return base
     # accuracy: a batch of the stratified subsample from its initial state to
-    # t_acc (its own autotuned tiles), each instance replayed by the oracle
+    # each horizon (its own autotuned tiles), each instance replayed by the
+    # oracle with its accepted step sizes
     sample = [i for idx in shapes.values() for i in idx[:acc_per_shape]]
     ba = mm.Batch([specs[i] for i in sample], device=local_rank)
     for j, i in enumerate(sample):
         ba.set_m(j, m0s[i])
-    ba.run(t_acc)
-    jobs = [(specs[i], m0s[i], ba.get_dt_history(j), ba.get_m(j)) for j, i in enumerate(sample)]
+    jobs, horizons = [], []
+    for t_h in t_acc:
+        ba.run(t_h)
+        horizons.append((t_h, [ba.get_stats(j)["accepted"] for j in range(len(sample))]))
+        jobs += [(specs[i], m0s[i], ba.get_dt_history(j), ba.get_m(j)) for j, i in enumerate(sample)]
     ba.close()
     with single_threaded_children(), mp.get_context("spawn").Pool(min(len(jobs), host_description()["nproc"])) as pool:
-        errs = pool.starmap(_replay_instance, jobs)
-    acc = {"t_end_s": t_acc, "instances": len(sample), "max_abs_m_err": max(errs),
-           "median_abs_m_err": float(np.median(errs)), "bar": 1e-5,
-           "per_shape_max": {f"{k[0]}x{k[1]}x{k[2]}": max(e for i, e in zip(sample, errs) if i in idx[:acc_per_shape])
-                             for k, idx in shapes.items()},
-           "method": "a batch of the subsample (8 instances per grid size, the first of each size) run from "
-                     "its initial state to t_end_s; the float64 oracle replays each instance's accepted step sizes"}
+        all_errs = pool.starmap(_replay_instance, jobs)
+    acc = {"instances": len(sample), "bar": 1e-5,
+           "method": f"a batch of the subsample ({acc_per_shape} instances per grid size, the first of each size) "
+                     "run from its initial state to each horizon; the float64 oracle replays each instance's "
+                     "accepted step sizes; max |m_gpu - m_oracle| per instance"}
+    for h, (t_h, steps) in enumerate(horizons):
+        errs = all_errs[h * len(sample):(h + 1) * len(sample)]
+        acc[f"t_{t_h * 1e12:g}ps"] = {
+            "accepted_steps_mean": float(np.mean(steps)), "max_abs_m_err": max(errs),
+            "median_abs_m_err": float(np.median(errs)),
+            "per_shape_max": {f"{k[0]}x{k[1]}x{k[2]}": max(e for i, e in zip(sample, errs) if i in idx[:acc_per_shape])
+                              for k, idx in shapes.items()}}
     seq_time = 0.0
     for key, idx in shapes.items():
         per = []
@@ -628,13 +682,12 @@ def run_batch(args, local_rank, t_end=0.1e-9, seq_per_shape=2, acc_per_shape=8, 
             per.append(time.perf_counter() - ts)
             ctx.close()
         seq_time += np.mean(per) * len(idx)
-    return {"workload": "batch512 (32x32x1, 64x32x1, 128x64x2, 96x96x4; 4 nm cells)", "instances": len(specs),
-            "t_end_s": t_end, "wall_s": wall, "instances_per_s": len(specs) / wall,
-            "cell_steps_per_s": cell_steps / wall, "accepted_steps_mean": float(np.mean([s["accepted"] for s in stats])),
-            "sequential_instances_per_s": len(specs) / seq_time,
-            "speedup_vs_sequential": seq_time / wall,
-            "sequential_sample": f"{seq_per_shape} instances per grid size, same t_end, extrapolated by count",
-            "accuracy_vs_oracle": acc, "autotuned_tiles": tiles}
+    base.update({"sequential_instances_per_s": len(specs) / seq_time,
+                 "speedup_vs_sequential": seq_time / wall,
+                 "sequential_sample": f"{seq_per_shape} instances per grid size on one GPU, same t_end, "
+                                      f"extrapolated by count",
+                 "accuracy_vs_oracle": acc})
+    return base
 
 
 def run_surrogate(args, local_rank, steps=40):
@@ -735,8 +788,8 @@ def main():
     ap.add_argument("--no-side", dest="side", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false")
-    ap.add_argument("--pairs", type=int, default=256, help="surrogate training pairs (the full recipe: 20000)")
-    ap.add_argument("--epochs", type=int, default=2, help="surrogate training epochs")
+    ap.add_argument("--pairs", type=int, default=20000, help="surrogate training pairs (the recipe: 20000)")
+    ap.add_argument("--epochs", type=int, default=1, help="surrogate training epochs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = env_rank()

@@ -191,39 +191,31 @@ __global__ void __launch_bounds__(kZNT, kZMinBlocks) k_zk(Geom g, float2* __rest
   for (int l = 0; l < LZH; ++l) sA[(c * PZ + 2 * l + rz) * CP + col] = v[l];
   __syncthreads();
   // 2. the kernel product B_i = sum_j K_ij A_j at every (kz, column) point of
-  //    the block, all three components per point, in place in sA; point q:
-  //    column q % 32, kz = q / 32 (consecutive lanes on consecutive columns:
-  //    conflict-free shared memory, coalesced octant rows).  The octant holds
-  //    K at (|ky|, |kz|): Kxy is odd in ky, Kxz in kz, Kyz in both.
+  //    the block, all three components per point, in place in sA.  Thread t
+  //    takes column t % 16 and kz = t / 16 + KZS k (KZS = threads / 16), so
+  //    the column, its mirror sign and octant row are per-thread constants;
+  //    a half-warp covers 16 consecutive columns (conflict-free shared
+  //    memory, 64-byte octant rows).  The octant holds K at (|ky|, |kz|):
+  //    Kxy is odd in ky, Kxz in kz, Kyz in both.
   {
-    constexpr int NPTS = PZ * kZCols;
-    constexpr int NPT = (NPTS + kZNT - 1) / kZNT;   // points per thread
+    constexpr int KZS = kZNT / kZCols;              // kz stride between a thread's points
+    constexpr int NPT = (PZ + KZS - 1) / KZS;       // points per thread (the last may be empty)
     constexpr int CH = 4;                           // points whose loads are issued together
+    const int pc = threadIdx.x % kZCols, kz0 = threadIdx.x / kZCols;
+    const int pky = blockIdx.x * kZCols + pc;
+    const bool my = pky > PY / 2;
+    const float sgy = my ? -1.f : 1.f;
     const int per = g.hky * g.hkz;                  // octant: 6 hkx hky hkz < 2^31 floats
-    const float* __restrict__ kpx = kt + kx * 6 * per;
+    const float* __restrict__ kb = kt + kx * 6 * per + (my ? PY - pky : pky);
 #pragma unroll
     for (int k0 = 0; k0 < NPT; k0 += CH) {
       float kc[CH][6];
       float2 A[CH][3];
-      float sgy[CH], sgz[CH];
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
-        const int q = threadIdx.x + (k0 + u) * kZNT;
-        if (k0 + u >= NPT || (NPTS % kZNT != 0 && q >= NPTS)) continue;
-        const int pc = q % kZCols, kz = q / kZCols;
-        const int pky = blockIdx.x * kZCols + pc;
-        int iy = pky, iz = kz;
-        sgy[u] = 1.f;
-        sgz[u] = 1.f;
-        if (pky > PY / 2) {
-          iy = PY - pky;
-          sgy[u] = -1.f;
-        }
-        if (kz > PZ / 2) {
-          iz = PZ - kz;
-          sgz[u] = -1.f;
-        }
-        const float* __restrict__ kq = kpx + iz * g.hky + iy;
+        const int kz = kz0 + (k0 + u) * KZS;
+        if (k0 + u >= NPT || (PZ % KZS != 0 && kz >= PZ)) continue;
+        const float* __restrict__ kq = kb + (kz > PZ / 2 ? PZ - kz : kz) * g.hky;
 #pragma unroll
         for (int t = 0; t < 6; ++t) kc[u][t] = __ldg(kq + t * per);
 #pragma unroll
@@ -231,11 +223,11 @@ __global__ void __launch_bounds__(kZNT, kZMinBlocks) k_zk(Geom g, float2* __rest
       }
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
-        const int q = threadIdx.x + (k0 + u) * kZNT;
-        if (k0 + u >= NPT || (NPTS % kZNT != 0 && q >= NPTS)) continue;
-        const int pc = q % kZCols, kz = q / kZCols;
+        const int kz = kz0 + (k0 + u) * KZS;
+        if (k0 + u >= NPT || (PZ % KZS != 0 && kz >= PZ)) continue;
+        const float sgz = kz > PZ / 2 ? -1.f : 1.f;
         const float kxx = kc[u][0], kyy = kc[u][1], kzz = kc[u][2];
-        const float kxy = sgy[u] * kc[u][3], kxz = sgz[u] * kc[u][4], kyz = sgy[u] * sgz[u] * kc[u][5];
+        const float kxy = sgy * kc[u][3], kxz = sgz * kc[u][4], kyz = sgy * sgz * kc[u][5];
         const float2 X = A[u][0], Y = A[u][1], Zc = A[u][2];
         sA[kz * CP + pc] = make_float2(kxx * X.x + kxy * Y.x + kxz * Zc.x, kxx * X.y + kxy * Y.y + kxz * Zc.y);
         sA[(PZ + kz) * CP + pc] =
