@@ -1370,6 +1370,7 @@ int mm_set_yz_kernels(mm_ctx* c, int which, int* active) {
     return fail(MM_ERR_ARG, "the three-kernel (y, z) path needs open y and z axes, py >= 32 and 16 <= pz <= 64");
   MM_CUDA(cudaStreamSynchronize(c->stream));
   c->yz_req = which;
+  c->graph_valid = false;   // the captured attempt holds the previous kernels
   const int rc = apply_yz_choice(c);
   if (rc) return rc;
   if (c->yz3) {
