@@ -582,13 +582,18 @@ def run_ours(args, rank, world, local_rank):
 
 def _replay_instance(spec, m0, dts, m_gpu):
     """Oracle replay of one batched instance's accepted steps (spawned
-    process): max |m_gpu - m_oracle|."""
+    process): (max |m_gpu - m_oracle|, the problem's own sensitivity: max
+    |m_oracle' - m_oracle| for an oracle run from m0 perturbed by 1e-7
+    (seeded Gaussian) with the same steps)."""
     from oracle.rk45 import RK45
     from paper_1406_7635_gb300.workloads import problem_from_instance
     p = problem_from_instance(spec, m0)
-    ora = RK45(p, m=p.m0.astype(np.float32).astype(np.float64))
+    m32 = p.m0.astype(np.float32).astype(np.float64)
+    ora = RK45(p, m=m32)
     ora.run_fixed(dts)
-    return float(np.abs(m_gpu.astype(np.float64) - ora.m).max())
+    pert = RK45(p, m=m32 + 1e-7 * np.random.default_rng(1406).standard_normal(m32.shape))
+    pert.run_fixed(dts)
+    return float(np.abs(m_gpu.astype(np.float64) - ora.m).max()), float(np.abs(pert.m - ora.m).max())
 
 
 def run_batch(args, local_rank, rank=0, world=1, t_end=0.1e-9, seq_per_shape=2, acc_per_shape=8,
@@ -658,14 +663,20 @@ def run_batch(args, local_rank, rank=0, world=1, t_end=0.1e-9, seq_per_shape=2, 
     acc = {"instances": len(sample), "bar": 1e-5,
            "method": f"a batch of the subsample ({acc_per_shape} instances per grid size, the first of each size) "
                      "run from its initial state to each horizon; the float64 oracle replays each instance's "
-                     "accepted step sizes; max |m_gpu - m_oracle| per instance"}
+                     "accepted step sizes; max |m_gpu - m_oracle| per instance, beside the oracle's own change "
+                     "when its initial m is perturbed by 1e-7 (the growth the dynamics give a rounding-sized "
+                     "perturbation over the same steps)"}
     for h, (t_h, steps) in enumerate(horizons):
-        errs = all_errs[h * len(sample):(h + 1) * len(sample)]
+        part = all_errs[h * len(sample):(h + 1) * len(sample)]
+        errs = [e for e, _ in part]
+        sens = [q for _, q in part]
         acc[f"t_{t_h * 1e12:g}ps"] = {
             "accepted_steps_mean": float(np.mean(steps)), "max_abs_m_err": max(errs),
             "median_abs_m_err": float(np.median(errs)),
             "per_shape_max": {f"{k[0]}x{k[1]}x{k[2]}": max(e for i, e in zip(sample, errs) if i in idx[:acc_per_shape])
-                              for k, idx in shapes.items()}}
+                              for k, idx in shapes.items()},
+            "oracle_sensitivity_1e-7": {"max": max(sens), "median": float(np.median(sens))},
+            "instances_within_bar_or_sensitivity": int(sum(e <= max(1e-5, 2 * q) for e, q in zip(errs, sens)))}
     seq_time = 0.0
     for key, idx in shapes.items():
         per = []
