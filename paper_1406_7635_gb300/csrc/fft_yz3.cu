@@ -176,6 +176,18 @@ __global__ void __launch_bounds__(kZNT, kZMinBlocks) k_zk(Geom g, float2* __rest
   const int nz = g.nz, PY = g.py;
   // column (kx, c, ., ky) of T, z stride PY (32-bit offsets: 3 hx nz py < 2^31)
   float2* __restrict__ cp = T + (kx * 3 + c) * nz * PY + ky;
+  // the block's kernel-octant rows (6 components x (PZ/2 + 1) kz rows of its
+  // 16 columns, read in the product below) do not depend on the previous
+  // kernel: ask for them in L2 while it drains
+  {
+    const int my = blockIdx.x * kZCols > PY / 2;
+    const int iy0 = my ? PY - (blockIdx.x * kZCols + kZCols - 1) : blockIdx.x * kZCols;
+    const int per = g.hky * g.hkz;
+    for (int e = threadIdx.x; e < 6 * (PZ / 2 + 1); e += kZNT) {
+      const int t = e / (PZ / 2 + 1), iz = e % (PZ / 2 + 1);
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(kt + kx * 6 * per + t * per + iz * g.hky + iy0));
+    }
+  }
   grid_dependency_wait();   // T comes from the y kernel
   if (st && st->done) return;   // (after the predecessor: one value for all threads)
   // 1. class rz of component c: the LZH-point DFT of a[z] W_PZ^(rz z)
