@@ -270,6 +270,159 @@ __global__ void __launch_bounds__(kZNT, kZMinBlocks) k_zk(Geom g, float2* __rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident y kernels for rows of PH = 64, 128, 256 points: a row is
+// held by G = PH / 16 lanes, 16 values each (y = j + G r, lane j), so the
+// PH-point transform is one 16-point DFT per lane over r, a twiddle, a
+// transpose through a per-warp shared buffer, and 16 / G G-point DFTs per
+// lane:  X[k1 + 16 k2] = sum_j W_G^(j k2) W_PH^(j k1) sum_r x[j + G r] W_16^(r k1).
+// No block barrier: the lanes of a row belong to one warp.  Lane j' of a
+// row ends with the outputs k1 = j' + G h (h < 16 / G), k2 < G, so stores
+// of consecutive lanes are consecutive.  Both parity classes of a row are
+// done by the same lanes (the class-1 input is x W_(2 PH)^y).
+// ---------------------------------------------------------------------------
+constexpr int kY2NT = 64;   // two warps per block
+
+template <int PH>
+struct Y2Cfg {
+  static constexpr int G = PH / 16;          // lanes per row
+  static constexpr int H = 16 / G;           // k1 values per lane
+  static constexpr int RPW = 32 / G;         // rows per warp
+  static constexpr int ROWS = RPW * (kY2NT / 32);
+  static constexpr int EP = 17;              // exchange pitch of one lane's 16 values
+  static constexpr int EW = RPW * G * EP;    // exchange buffer per warp (complex values)
+};
+
+template <int PH>
+__global__ void __launch_bounds__(kY2NT, 11) k_yf2(Geom g, const float2* __restrict__ spec, float2* __restrict__ T,
+                                                   const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  using Y = Y2Cfg<PH>;
+  constexpr int G = Y::G, H = Y::H, EP = Y::EP;
+  __shared__ float2 twh[PH], twc[PH];   // W_PH^i and the class-1 twiddle W_(2 PH)^y
+  __shared__ float2 ex[(kY2NT / 32) * Y::EW];
+  twiddles_async<kY2NT>(twh, tw, PH, kTwN / PH);
+  twiddles_async<kY2NT>(twc, tw, PH, kTwN / (2 * PH));
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rw = lane / G, j = lane % G;                  // row of the warp, lane of the row
+  const int c = blockIdx.y, kx = blockIdx.z;
+  const int z = blockIdx.x * Y::ROWS + warp * Y::RPW + rw;
+  const int ny = g.ny, nz = g.nz;
+  float2* e = ex + warp * Y::EW + rw * G * EP;          // this row's exchange area [j][k1]
+  grid_dependency_wait();   // the spectrum comes from the previous kernel
+  if (st && st->done) return;   // (after the predecessor: one value for all threads)
+  const float2* __restrict__ src = spec + ((c * g.hx + kx) * nz + (z < nz ? z : 0)) * ny;
+  float2* __restrict__ dst = T + ((kx * 3 + c) * nz + (z < nz ? z : 0)) * (2 * PH);
+#pragma unroll
+  for (int cls = 0; cls < 2; ++cls) {
+    // (the row is read again for class 1, from L1, rather than held in
+    // registers across the class-0 transform)
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int y = j + G * r;
+      const float2 x = (z < nz && y < ny) ? src[y] : make_float2(0.f, 0.f);
+      v[r] = cls ? cmul(x, twc[y]) : x;
+    }
+    Dft<16, -1>::run(v);                                  // v[k1] = sum_r x W_16^(r k1)
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], twh[(j * k1) & (PH - 1)]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) e[j * EP + k1] = v[k1];
+    __syncwarp();
+    float2 w[H][G];
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int jj = 0; jj < G; ++jj) w[h][jj] = e[jj * EP + j + G * h];
+    __syncwarp();   // the buffer is free for the next class
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      Dft<G, -1>::run(w[h]);                              // w[h][k2] = X(k1 + 16 k2), k1 = j + G h
+      if (z < nz) {
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) dst[2 * (j + G * h + 16 * k2) + cls] = w[h][k2];
+      }
+    }
+  }
+}
+
+template <int PH>
+__global__ void __launch_bounds__(kY2NT, 11) k_yi2(Geom g, const float2* __restrict__ T, float2* __restrict__ spec,
+                                                   const float2* __restrict__ tw, const DevState* __restrict__ st) {
+  using Y = Y2Cfg<PH>;
+  constexpr int G = Y::G, H = Y::H, EP = Y::EP;
+  __shared__ float2 twh[PH], twc[PH];
+  __shared__ float2 ex[(kY2NT / 32) * Y::EW];
+  twiddles_async<kY2NT>(twh, tw, PH, kTwN / PH);
+  twiddles_async<kY2NT>(twc, tw, PH, kTwN / (2 * PH));
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rw = lane / G, j = lane % G;
+  const int c = blockIdx.y, kx = blockIdx.z;
+  const int z = blockIdx.x * Y::ROWS + warp * Y::RPW + rw;
+  const int ny = g.ny, nz = g.nz;
+  float2* e = ex + warp * Y::EW + rw * G * EP;
+  grid_dependency_wait();   // T comes from the column kernel
+  if (st && st->done) return;   // (after the predecessor: one value for all threads)
+  const float2* __restrict__ src = T + ((kx * 3 + c) * nz + (z < nz ? z : 0)) * (2 * PH);
+  float2 x0[16];
+#pragma unroll
+  for (int cls = 0; cls < 2; ++cls) {
+    // lane j holds X(k1 + 16 k2) for k1 = j + G h: inverse over k2 first
+    float2 w[H][G];
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2)
+        w[h][k2] = z < nz ? src[2 * (j + G * h + 16 * k2) + cls] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      Dft<G, 1>::run(w[h]);                               // w[h][jj] = V(jj, k1)
+#pragma unroll
+      for (int jj = 0; jj < G; ++jj) {
+        const int k1 = j + G * h;
+        e[jj * EP + k1] = (jj && k1) ? cmul(w[h][jj], cconj(twh[(jj * k1) & (PH - 1)])) : w[h][jj];
+      }
+    }
+    __syncwarp();
+    float2 v[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) v[k1] = e[j * EP + k1];
+    __syncwarp();   // the buffer is free for the next class
+    Dft<16, 1>::run(v);                                   // v[r] = x_cls(j + G r)
+    if (cls == 0) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) x0[r] = v[r];
+    } else if (z < nz) {
+      float2* __restrict__ out = spec + ((c * g.hx + kx) * nz + z) * ny;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int y = j + G * r;
+        if (y < ny) out[y] = cadd(x0[r], cmul(v[r], cconj(twc[y])));
+      }
+    }
+  }
+}
+
+template <int PH>
+void run_y2(const Geom& g, const Buffers& b, float2* T, bool forward, cudaStream_t s) {
+  using Y = Y2Cfg<PH>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((g.nz + Y::ROWS - 1) / Y::ROWS, 3, g.hx);
+  cfg.blockDim = dim3(kY2NT);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (forward) cudaLaunchKernelEx(&cfg, k_yf2<PH>, g, (const float2*)b.spec, T, (const float2*)b.tw, (const DevState*)b.st);
+  else cudaLaunchKernelEx(&cfg, k_yi2<PH>, g, (const float2*)T, b.spec, (const float2*)b.tw, (const DevState*)b.st);
+}
+
 template <int PH>
 void run_y(const Geom& g, const float2* spec_in, float2* T, float2* spec_out, const float2* tw, const DevState* st,
            cudaStream_t s, bool forward) {
@@ -315,9 +468,9 @@ void launch_y(const Geom& g, const Buffers& b, float2* T, bool forward, cudaStre
   switch (g.py / 2) {
     case 16: run_y<16>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
     case 32: run_y<32>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
-    case 64: run_y<64>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
-    case 128: run_y<128>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
-    case 256: run_y<256>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
+    case 64: run_y2<64>(g, b, T, forward, s); break;
+    case 128: run_y2<128>(g, b, T, forward, s); break;
+    case 256: run_y2<256>(g, b, T, forward, s); break;
     case 512: run_y<512>(g, in, T, b.spec, b.tw, b.st, s, forward); break;
     default: break;
   }

@@ -52,8 +52,9 @@ def grid_problem(shape, seed):
 
 
 # (nz, ny, nx): pz = 16 with py = 64; pz = 32 with py = 128 and odd ny; pz = 64
-# with py = 256 and ny below 128 (the smoke grid); nz = 20 < 32 with pz = 64
-SHAPES = [(8, 20, 24), (12, 47, 40), (32, 78, 68), (20, 64, 36)]
+# with py = 256 and ny below 128 (the smoke grid); nz = 20 < 32 with pz = 64;
+# py = 512 (rows of 256 points per parity class) with ny = 130
+SHAPES = [(8, 20, 24), (12, 47, 40), (32, 78, 68), (20, 64, 36), (16, 130, 24)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
