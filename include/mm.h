@@ -303,13 +303,15 @@ int mm_profile_attempts(mm_ctx* ctx, int attempts, int max, int* kinds, double* 
  * the same convolution, up to float32 rounding): which = 0 the grid's
  * default (2 where available, else 1), 1 one thread-block cluster per kx
  * plane (the (ky, kz) plane split into frequency residue classes across the
- * cluster's blocks, summed through distributed shared memory), 2 three
- * kernels over a y-transformed buffer of 24 B per (kx, z, ky) point (y
- * forward; per (kx, ky) column z forward, kernel product and z inverse;
- * y inverse).  2 needs open y and z axes, py >= 32 and 16 <= pz <= 64
- * (MM_ERR_ARG otherwise).  *active (may be NULL) receives the kernels in use:
- * 1 or 2, or 0 on a grid without the fused layout.  The stepping graph is
- * captured again at the next step. */
+ * cluster's blocks, summed through distributed shared memory), 2 the
+ * register-resident kernels: on 3-D grids three kernels over a y-transformed
+ * buffer of 24 B per (kx, z, ky) point (y forward; per (kx, ky) column z
+ * forward, kernel product and z inverse; y inverse), on 2-D grids one kernel
+ * per kx plane (y forward, kernel product, y inverse).  2 needs open y and z
+ * axes and, in 3-D, py >= 32 and 16 <= pz <= 64, in 2-D (one layer) py of
+ * 128, 256 or 512 (MM_ERR_ARG otherwise).  *active (may be NULL) receives the
+ * kernels in use: 1 or 2, or 0 on a grid without the fused layout.  The
+ * stepping graph is captured again at the next step. */
 int mm_set_yz_kernels(mm_ctx* ctx, int which, int* active);
 
 /* FP32 fused multiply-add throughput of `device` (no counterpart in the

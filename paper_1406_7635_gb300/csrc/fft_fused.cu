@@ -844,6 +844,17 @@ void launch_demag_fused3(const Geom& g, const Buffers& b, const float* m, float2
 #undef CALL_IX
 }
 
+void launch_demag_fused2d(const Geom& g, const Buffers& b, const float* m, cudaStream_t s) {
+  const BatchArgs ba{1, nullptr, nullptr, 0};
+#define CALL_FX(LL) run_fx_t<LL>(g, b, m, s, ba)
+  MM_ROWL(g.lx, CALL_FX)
+#undef CALL_FX
+  launch_demag_y2d(g, b, s);
+#define CALL_IX(LL) run_ix_t<LL>(g, b, s, ba)
+  MM_ROWL(g.lx, CALL_IX)
+#undef CALL_IX
+}
+
 static void launch_yz_batch(const Geom& g, const Buffers& b, cudaStream_t s, const BatchArgs& ba, bool pdl) {
   const int key = g.ly * 100 + g.lz;
   switch (key) {

@@ -423,6 +423,129 @@ void run_y2(const Geom& g, const Buffers& b, float2* T, bool forward, cudaStream
   else cudaLaunchKernelEx(&cfg, k_yi2<PH>, g, (const float2*)T, b.spec, (const float2*)b.tw, (const DevState*)b.st);
 }
 
+// ---------------------------------------------------------------------------
+// 2-D grids (pz = 1): the y transform, the kernel product and the inverse y
+// transform of one kx plane in one block, with the register-resident y
+// transforms above.  Six rows (3 components x 2 parity classes) of G = PH/16
+// lanes each; the forward spectra meet in shared memory for the product,
+// and the two classes of a component (G lanes apart) combine by a shuffle.
+// ---------------------------------------------------------------------------
+template <int PH>
+struct Y2dCfg {
+  static constexpr int G = PH / 16, H = 16 / G, RPW = 32 / G, EP = 17;
+  static constexpr int NT = (6 * G + 31) / 32 * 32;   // rows 6 and up (G = 8: 16 lanes) idle
+  static constexpr int NW = NT / 32;
+};
+
+template <int PH>
+__global__ void __launch_bounds__(Y2dCfg<PH>::NT) k_y2d(Geom g, float2* __restrict__ spec,
+                                                        const float* __restrict__ kt,
+                                                        const float2* __restrict__ tw,
+                                                        const DevState* __restrict__ st) {
+  using Y = Y2dCfg<PH>;
+  constexpr int G = Y::G, H = Y::H, EP = Y::EP, PY = 2 * PH;
+  __shared__ float2 twh[PH], twc[PH];
+  __shared__ float2 ex[Y::NW * Y::RPW * G * EP];
+  __shared__ float2 S[3 * PY];   // [component][class][k]: the spectrum at ky = 2 k + class
+  twiddles_async<Y::NT>(twh, tw, PH, kTwN / PH);
+  twiddles_async<Y::NT>(twc, tw, PH, kTwN / PY);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = threadIdx.x / G, j = threadIdx.x % G;   // row = 2 c + class
+  const bool act = row < 6;
+  const int c = act ? row >> 1 : 0, cls = row & 1;
+  const int kx = blockIdx.x, ny = g.ny;
+  float2* e = ex + (warp * Y::RPW + lane / G) * G * EP;
+  grid_dependency_wait();   // the spectrum comes from the previous kernel
+  if (st && st->done) return;   // (after the predecessor: one value for all threads)
+  float2* __restrict__ rowp = spec + (c * g.hx + kx) * ny;   // nz = 1: row (c, kx)
+  // 1. forward y of class cls of component c: X(k1 + 16 k2), k1 = j + G h
+  {
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int y = j + G * r;
+      const float2 x = (act && y < ny) ? rowp[y] : make_float2(0.f, 0.f);
+      v[r] = cls ? cmul(x, twc[y]) : x;
+    }
+    Dft<16, -1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], twh[(j * k1) & (PH - 1)]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) e[j * EP + k1] = v[k1];
+    __syncwarp();
+    float2 w[H][G];
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int jj = 0; jj < G; ++jj) w[h][jj] = e[jj * EP + j + G * h];
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      Dft<G, -1>::run(w[h]);
+      if (act) {
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) S[row * PH + j + G * h + 16 * k2] = w[h][k2];
+      }
+    }
+  }
+  __syncthreads();
+  // 2. kernel product at every ky (kz = 0): Kxy is odd in ky; Kxz and Kyz
+  //    (odd in kz) enter with their stored values
+  {
+    const int per = g.hky * g.hkz;   // octant: 6 hkx hky hkz < 2^31 floats
+    const float* __restrict__ kb = kt + kx * 6 * per;
+    for (int q = threadIdx.x; q < PY; q += Y::NT) {
+      const int qc = q / PH, k = q % PH, ky = 2 * k + qc;
+      const int iy = ky > PH ? PY - ky : ky;
+      const float sy = ky > PH ? -1.f : 1.f;
+      float kc[6];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) kc[t] = __ldg(kb + t * per + iy);
+      const float kxx = kc[0], kyy = kc[1], kzz = kc[2], kxy = sy * kc[3], kxz = kc[4], kyz = sy * kc[5];
+      const float2 X = S[(0 + qc) * PH + k], Yv = S[(2 + qc) * PH + k], Z = S[(4 + qc) * PH + k];
+      S[(0 + qc) * PH + k] = make_float2(kxx * X.x + kxy * Yv.x + kxz * Z.x, kxx * X.y + kxy * Yv.y + kxz * Z.y);
+      S[(2 + qc) * PH + k] = make_float2(kxy * X.x + kyy * Yv.x + kyz * Z.x, kxy * X.y + kyy * Yv.y + kyz * Z.y);
+      S[(4 + qc) * PH + k] = make_float2(kxz * X.x + kyz * Yv.x + kzz * Z.x, kxz * X.y + kyz * Yv.y + kzz * Z.y);
+    }
+  }
+  __syncthreads();
+  // 3. inverse y of the class, then x[y] = x_0[y] + conj(W_PY^y) x_1[y]: the
+  //    class-0 lane writes r < 8, the class-1 lane (G lanes up) r >= 8
+  float2 v[16];
+  {
+    float2 w[H][G];
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) w[h][k2] = act ? S[row * PH + j + G * h + 16 * k2] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      Dft<G, 1>::run(w[h]);
+#pragma unroll
+      for (int jj = 0; jj < G; ++jj) {
+        const int k1 = j + G * h;
+        e[jj * EP + k1] = (jj && k1) ? cmul(w[h][jj], cconj(twh[(jj * k1) & (PH - 1)])) : w[h][jj];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) v[k1] = e[j * EP + k1];
+    Dft<16, 1>::run(v);   // v[r] = x_class(j + G r)
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 send = cls ? v[i] : v[i + 8];
+    const float2 recv =
+        make_float2(__shfl_xor_sync(0xffffffffu, send.x, G), __shfl_xor_sync(0xffffffffu, send.y, G));
+    const int r = cls ? i + 8 : i, y = j + G * r;
+    const float2 w = cconj(twc[y]);
+    const float2 out = cls ? cadd(recv, cmul(v[i + 8], w)) : cadd(v[i], cmul(recv, w));
+    if (act && y < ny) rowp[y] = out;
+  }
+}
+
 template <int PH>
 void run_y(const Geom& g, const float2* spec_in, float2* T, float2* spec_out, const float2* tw, const DevState* st,
            cudaStream_t s, bool forward) {
@@ -477,6 +600,38 @@ void launch_y(const Geom& g, const Buffers& b, float2* T, bool forward, cudaStre
 }
 
 }  // namespace
+
+// The one-kernel 2-D plan: a fused spectrum layout of a single layer with an
+// open y axis padded to 128, 256 or 512 points.
+bool y2d_plan(const Geom& g) {
+  return g.fused && g.pz == 1 && g.nz == 1 && g.pbcy == 0 && (g.py == 128 || g.py == 256 || g.py == 512);
+}
+
+void launch_demag_y2d(const Geom& g, const Buffers& b, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g.hx);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (g.py) {
+    case 128:
+      cfg.blockDim = dim3(Y2dCfg<64>::NT);
+      cudaLaunchKernelEx(&cfg, k_y2d<64>, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st);
+      break;
+    case 256:
+      cfg.blockDim = dim3(Y2dCfg<128>::NT);
+      cudaLaunchKernelEx(&cfg, k_y2d<128>, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st);
+      break;
+    case 512:
+      cfg.blockDim = dim3(Y2dCfg<256>::NT);
+      cudaLaunchKernelEx(&cfg, k_y2d<256>, g, b.spec, (const float*)b.ktf, (const float2*)b.tw, (const DevState*)b.st);
+      break;
+    default: break;
+  }
+}
 
 // The three-kernel plan: a fused spectrum layout, open (padded) y and z axes
 // with 32 <= py <= 1024 and 16 <= pz <= 64 (z classes of 8, 16 or 32 points).

@@ -71,6 +71,7 @@ struct mm_ctx {
   RsMaps maps{};                 // tensor maps of the row-stage kernels (rowstage_maps)
   int yz_req = 0;                // requested (y, z) kernels: 0 default, 1 cluster, 2 three kernels
   bool yz3 = false;              // the three-kernel (y, z) path is active
+  bool y2d = false;              // the one-kernel 2-D (y, K, y^-1) path is active
   float2* yzt = nullptr;         // its y-transformed buffer (yz3_bytes)
   SttLUT* stt_lut = nullptr;     // device table
   int method = 0;                // host copy of DevState::method
@@ -215,12 +216,14 @@ int demag_launches(const mm_ctx* c) {
 // possibly without the device state)
 void demag_exact(mm_ctx* c, const Buffers& nb, const float* m) {
   if (c->yz3) launch_demag_fused3(c->g, nb, m, c->yzt, c->stream);
+  else if (c->y2d) launch_demag_fused2d(c->g, nb, m, c->stream);
   else launch_demag(c->g, nb, m, c->stream);
 }
 
 // the (y, z) part of the convolution inside the row-stage path
 void demag_yz(mm_ctx* c) {
   if (c->yz3) launch_demag_yz3(c->g, c->b, c->yzt, c->stream);
+  else if (c->y2d) launch_demag_y2d(c->g, c->b, c->stream);
   else launch_demag_yz(c->g, c->b, c->stream);
 }
 
@@ -243,6 +246,9 @@ int apply_yz_choice(mm_ctx* c) {
   }
   if (want != c->yz3) c->graph_valid = false;
   c->yz3 = want;
+  const bool want2d = y2d_plan(c->g) && c->yz_req != 1;
+  if (want2d != c->y2d) c->graph_valid = false;
+  c->y2d = want2d;
   return MM_OK;
 }
 
@@ -923,6 +929,7 @@ int mm_set_pbc(mm_ctx* c, int px, int py, int pz) {
       c->yzt = nullptr;
     }
     c->yz3 = false;
+    c->y2d = false;
     const int rc = apply_yz_choice(c);
     if (rc) return rc;
     // one convolution outside any capture (launch attributes), as at creation
@@ -1366,14 +1373,15 @@ int mm_sync(mm_ctx* c) {
 int mm_set_yz_kernels(mm_ctx* c, int which, int* active) {
   if (!c) return fail(MM_ERR_ARG, "ctx is NULL");
   if (which < 0 || which > 2) return fail(MM_ERR_ARG, "which must be 0 (default), 1 (cluster) or 2 (three kernels)");
-  if (which == 2 && !yz3_plan(c->g))
-    return fail(MM_ERR_ARG, "the three-kernel (y, z) path needs open y and z axes, py >= 32 and 16 <= pz <= 64");
+  if (which == 2 && !yz3_plan(c->g) && !y2d_plan(c->g))
+    return fail(MM_ERR_ARG, "the register-resident (y, z) kernels need open y and z axes and, in 3-D, py >= 32 and "
+                            "16 <= pz <= 64, in 2-D py of 128, 256 or 512");
   MM_CUDA(cudaStreamSynchronize(c->stream));
   c->yz_req = which;
   c->graph_valid = false;   // the captured attempt holds the previous kernels
   const int rc = apply_yz_choice(c);
   if (rc) return rc;
-  if (c->yz3) {
+  if (c->yz3 || c->y2d) {
     // one convolution outside any capture (launch attributes)
     Buffers nb = c->b;
     nb.st = nullptr;
@@ -1381,7 +1389,7 @@ int mm_set_yz_kernels(mm_ctx* c, int which, int* active) {
     MM_CUDA(cudaStreamSynchronize(c->stream));
     MM_CUDA(cudaGetLastError());
   }
-  if (active) *active = c->g.fused ? (c->yz3 ? 2 : 1) : 0;
+  if (active) *active = c->g.fused ? ((c->yz3 || c->y2d) ? 2 : 1) : 0;
   return MM_OK;
 }
 
@@ -1440,7 +1448,7 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
         launch_yz3_part(c->g, c->b, c->yzt, 2, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[q++], c->stream);
       } else if (c->T.demag) {
-        launch_demag_yz(c->g, c->b, c->stream);
+        demag_yz(c);
         e = cudaEventRecord(ev[q++], c->stream);
       }
       launch_rowstage(c->g, c->b, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);

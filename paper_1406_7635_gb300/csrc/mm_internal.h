@@ -189,6 +189,12 @@ void launch_demag_yz(const Geom& g, const Buffers& b, cudaStream_t s);
 // in place in T, y inverse back into the spectrum; yz3_plan(g) tells whether
 // the grid supports it.  launch_demag_fused3: the whole convolution with it.
 bool yz3_plan(const Geom& g);
+// 2-D grids: y forward, kernel product and y inverse of a kx plane in one
+// block (fft_yz3.cu), in place in the spectrum; y2d_plan(g) tells whether
+// the grid supports it.  launch_demag_fused2d: the whole convolution with it.
+bool y2d_plan(const Geom& g);
+void launch_demag_y2d(const Geom& g, const Buffers& b, cudaStream_t s);
+void launch_demag_fused2d(const Geom& g, const Buffers& b, const float* m, cudaStream_t s);
 size_t yz3_bytes(const Geom& g);
 void launch_demag_yz3(const Geom& g, const Buffers& b, float2* T, cudaStream_t s);
 void launch_demag_fused3(const Geom& g, const Buffers& b, const float* m, float2* T, cudaStream_t s);

@@ -1,8 +1,10 @@
 """The two implementations of the (y, z) part of the fused demag convolution
 (Sec. III.B) against the float64 oracle: the cluster kernel (one
 thread-block cluster per kx plane, residue classes across the cluster) and
-the three kernels (y forward into a y-transformed buffer; per (kx, ky)
-column z forward, kernel product and z inverse in registers; y inverse).
+the register-resident kernels (3-D: y forward into a y-transformed buffer;
+per (kx, ky) column z forward, kernel product and z inverse in registers; y
+inverse.  2-D: y forward, product and y inverse of a kx plane in one
+block).
 
 Grids cover every z class length of the column kernel (pz = 16, 32, 64),
 y rows of 64, 128 and 256 padded points, ny and nz below their class
@@ -54,7 +56,10 @@ def grid_problem(shape, seed):
 # (nz, ny, nx): pz = 16 with py = 64; pz = 32 with py = 128 and odd ny; pz = 64
 # with py = 256 and ny below 128 (the smoke grid); nz = 20 < 32 with pz = 64;
 # py = 512 (rows of 256 points per parity class) with ny = 130
-SHAPES = [(8, 20, 24), (12, 47, 40), (32, 78, 68), (20, 64, 36), (16, 130, 24)]
+SHAPES = [(8, 20, 24), (12, 47, 40), (32, 78, 68), (20, 64, 36), (16, 130, 24),
+          # 2-D films: the one-kernel (y, K, y^-1) path with rows of 64, 128
+          # and 256 points per class (odd ny, ny below the class length)
+          (1, 60, 100), (1, 97, 64), (1, 256, 256)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
