@@ -250,11 +250,17 @@ YZ_SOURCES = ("paper_1406_7635_gb300/csrc/fft_fused.cu", "paper_1406_7635_gb300/
 
 
 def sources_sha(files):
+    """Hash of the code of `files`: line comments and blank lines are left
+    out, so that a change of wording does not orphan counters taken on the
+    same kernels."""
     import hashlib
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

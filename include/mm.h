@@ -289,10 +289,12 @@ int mm_sync(mm_ctx* ctx);
  * (kinds[i]: 0 stage-input prep, 1 (y, z) demag convolution cluster kernel,
  * 2 row-stage kernel: x transforms, field, torque, stage update; with the
  * three-kernel (y, z) path 3 y forward, 4 column kernel: z forward, kernel
- * product, z inverse, 5 y inverse) and its mean duration over the attempts
- * in microseconds (us[i]).  The events keep each
- * kernel from overlapping its neighbour (no programmatic-dependent-launch
- * overlap), so the sum can exceed the graph's time per attempt.  L2 is not
+ * product, z inverse, 5 y inverse; 6 earlier-stage sums of the next row
+ * kernel) and its mean duration over the attempts in microseconds (us[i]).
+ * The events keep each kernel from overlapping its neighbour (no
+ * programmatic-dependent-launch overlap; the earlier-stage sums, a branch
+ * beside the (y, z) part in the graph, run in line here), so the sum can
+ * exceed the graph's time per attempt.  L2 is not
  * flushed between launches.  MM_ERR_STATE before set_m and unless the context
  * steps with the fused row-stage kernels (RK45, exact demag, no periodic x
  * axis, no spin-transfer torque); the controller's errors as mm_step. */

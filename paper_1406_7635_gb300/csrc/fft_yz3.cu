@@ -8,13 +8,18 @@
 //         forward (nz inputs, pz points), the kernel product B_i = K_ij M_j
 //         with the octant's mirror signs, z inverse cropped to z < nz, in
 //         place in T;
-//   k_yi  y inverse: T rows -> spectrum rows, cropped to y < ny.
+//   k_yi  y inverse: T rows -> spectrum rows, cropped to y < ny;
+//
+// and, for 2-D grids (pz = 1), k_y2d: y forward, kernel product and y
+// inverse of one kx plane in one block.
 //
 // Both transforms split their padded length by frequency parity: with
 // k = 2 j + r, the padded DFT restricted to class r is the half-length DFT of
 // x[n] W_P^(r n), exact because the inputs fill at most half the padded
-// length.  The y classes are two pencils per row, transformed by Stockham
-// passes in shared memory; the z classes are held in registers (pz / 2
+// length.  The y classes are two pencils per row: for 64..256 points per
+// class each pencil is held in the registers of PH / 16 lanes of one warp
+// (k_yf2 / k_yi2 / k_y2d), otherwise it is transformed by Stockham passes in
+// shared memory (k_yf / k_yi).  The z classes are held in registers (pz / 2
 // points per thread), one thread per (column, component, class), so the z
 // transforms need no shared-memory passes at all: the threads of a column
 // exchange only the spectra the product needs and, after the inverse, the

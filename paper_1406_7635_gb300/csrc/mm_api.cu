@@ -73,6 +73,10 @@ struct mm_ctx {
   bool yz3 = false;              // the three-kernel (y, z) path is active
   bool y2d = false;              // the one-kernel 2-D (y, K, y^-1) path is active
   float2* yzt = nullptr;         // its y-transformed buffer (yz3_bytes)
+  // branch of the row-stage path: the earlier-stage sums (k_rs_partial) run
+  // on `side`, forked after each row kernel and joined before the next
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   SttLUT* stt_lut = nullptr;     // device table
   int method = 0;                // host copy of DevState::method
   bool lut_dirty = true;
@@ -285,12 +289,45 @@ void enqueue_k1(mm_ctx* c) {
   launch_torque_t(c->g, c->b, c->T, c->stt, 0, c->freq, c->phase, c->stream);
 }
 
+// Whether the earlier-stage sums of the row kernels run as a graph branch
+// (k_rs_partial beside the (y, z) part) or inside the row kernels.  Same-GPU
+// A/B (ms per step, in-kernel -> branch): 128 x 128 x 32, row kernel in 1.7
+// waves, 0.4589 -> 0.4470 (row kernel 34.0 -> 27.8 us); 256 x 256 x 1 film,
+// one wave and a single short (y, z) kernel, 0.1609 -> 0.1649.  The rule is
+// the one of the row kernel's programmatic dependent launch: grids whose
+// (y, z) part runs in several waves.
+bool partial_branch(const mm_ctx* c) { return c->b.part && pdl_row(c->g); }
+
+// the buffers the row kernels get: without the branch, no partial sums
+Buffers row_buffers(const mm_ctx* c) {
+  Buffers b = c->b;
+  if (!partial_branch(c)) b.part = nullptr;
+  return b;
+}
+
+// The earlier-stage sums of stage s on the side stream, after everything
+// enqueued so far on the context's stream; the row kernel of stage s waits
+// for them (join_partial).
+void fork_partial(mm_ctx* c, int s) {
+  cudaEventRecord(c->ev_fork, c->stream);
+  cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  launch_rs_partial(c->g, c->b, s, s < 6 ? 1 : 2, c->side);
+  cudaEventRecord(c->ev_join, c->side);
+}
+void join_partial(mm_ctx* c) { cudaStreamWaitEvent(c->stream, c->ev_join, 0); }
+
 void enqueue_attempt(mm_ctx* c) {
   if (rowstage_path(c)) {
-    launch_rowstage(c->g, c->b, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
+    // stage s: [sums of stage s] beside [(y, z) part], then the row kernel
+    const bool br = partial_branch(c);
+    const Buffers rb = row_buffers(c);
+    if (br) fork_partial(c, 1);
+    launch_rowstage(c->g, rb, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
     for (int s = 1; s < 7; ++s) {
+      if (br && s > 1) fork_partial(c, s);
       if (c->T.demag) demag_yz(c);
-      launch_rowstage(c->g, c->b, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
+      if (br) join_partial(c);
+      launch_rowstage(c->g, rb, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
     }
     return;
   }
@@ -472,6 +509,10 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
     if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, cudaGetErrorString(e)));
     c->own_stream = true;
   }
+  e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(fail(MM_ERR_CUDA, cudaGetErrorString(e)));
   const size_t vec = 3 * (size_t)g.n * sizeof(float);
   Buffers& b = c->b;
   auto alloc = [&](void** p, size_t bytes) {
@@ -483,6 +524,7 @@ int mm_create(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double
   for (int j = 0; j < 7; ++j) alloc((void**)&b.k[j], vec);
   alloc((void**)&b.ms, vec);
   if (g.fused) alloc((void**)&b.ms2, vec);
+  if (g.fused) alloc((void**)&b.part, vec);
   alloc((void**)&b.bd, vec);
   alloc((void**)&b.out, vec);
   alloc((void**)&b.spec, 3 * (size_t)g.sc * sizeof(float2));
@@ -558,10 +600,16 @@ int mm_destroy(mm_ctx* c) {
   Buffers& b = c->b;
   void* ptrs[] = {b.m[0], b.m[1], b.k[0], b.k[1], b.k[2], b.k[3], b.k[4], b.k[5], b.k[6], b.ms, b.ms2, b.bd, b.out,
                   b.spec, b.kt, b.ktf, b.tw, b.mask, b.region, b.lut, b.xlut, b.code, b.st, b.hist, b.acc,
-                  b.fixed, c->sur_acc, c->stt_lut, c->yzt};
+                  b.fixed, c->sur_acc, c->stt_lut, c->yzt, b.part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return MM_OK;
@@ -903,12 +951,13 @@ int mm_set_pbc(mm_ctx* c, int px, int py, int pz) {
   MM_CUDA(cudaStreamSynchronize(c->stream));
   // buffers whose size depends on the transform lengths
   Buffers& b = c->b;
-  void* old[] = {b.spec, b.kt, b.ktf, b.ms2};
+  void* old[] = {b.spec, b.kt, b.ktf, b.ms2, b.part};
   for (void* p : old)
     if (p) cudaFree(p);
   b.spec = nullptr;
   b.kt = b.ktf = nullptr;
   b.ms2 = nullptr;
+  b.part = nullptr;
   c->graph_valid = false;
   c->k1_valid = false;
   const size_t vec = 3 * (size_t)g.n * sizeof(float);
@@ -918,6 +967,8 @@ int mm_set_pbc(mm_ctx* c, int px, int py, int pz) {
   if (e == cudaSuccess && g.fused) e = cudaMalloc((void**)&b.ktf, 6 * (size_t)g.hkx * g.hky * g.hkz * sizeof(float));
   if (e == cudaSuccess && g.fused) e = cudaMalloc((void**)&b.ms2, vec);
   if (e == cudaSuccess && g.fused) e = cudaMemsetAsync(b.ms2, 0, vec, c->stream);
+  if (e == cudaSuccess && g.fused) e = cudaMalloc((void**)&b.part, vec);
+  if (e == cudaSuccess && g.fused) e = cudaMemsetAsync(b.part, 0, vec, c->stream);
   if (e == cudaSuccess) e = build_kernel_spectrum(g, c->dx, c->dy, c->dz, b.kt, c->stream);
   if (e == cudaSuccess && g.fused) launch_kt_transpose(g, b.kt, b.ktf, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1400,7 +1451,8 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
   int rc = flush_luts(c);
   if (rc) return rc;
   // launch positions of one attempt: the prep kernel, then per stage the
-  // (y, z) kernel(s) (with demag) and the row kernel
+  // (y, z) kernel(s) (with demag), the earlier-stage sums (here in line, in
+  // the graph a branch beside the (y, z) part) and the row kernel
   std::vector<int> kind;
   kind.push_back(0);
   for (int s = 1; s < 7; ++s) {
@@ -1413,6 +1465,7 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
         kind.push_back(1);
       }
     }
+    if (partial_branch(c)) kind.push_back(6);
     kind.push_back(2);
   }
   const int P = (int)kind.size();
@@ -1434,6 +1487,7 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
   const bool k1_was_valid = c->k1_valid;
   if (!c->k1_valid) enqueue_k1(c);
   size_t q = 0;
+  const Buffers rb = row_buffers(c);
   cudaError_t e = cudaEventRecord(ev[q++], c->stream);
   for (int a = 0; a < attempts && e == cudaSuccess; ++a) {
     launch_rowstage(c->g, c->b, c->T, c->maps, 0, 1, 0, c->freq, c->phase, c->stream);
@@ -1451,7 +1505,11 @@ int mm_profile_attempts(mm_ctx* c, int attempts, int max, int* kinds, double* us
         demag_yz(c);
         e = cudaEventRecord(ev[q++], c->stream);
       }
-      launch_rowstage(c->g, c->b, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
+      if (partial_branch(c)) {
+        launch_rs_partial(c->g, c->b, s, s < 6 ? 1 : 2, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[q++], c->stream);
+      }
+      launch_rowstage(c->g, rb, c->T, c->maps, 1, s, s < 6 ? 1 : 2, c->freq, c->phase, c->stream);
       if (e == cudaSuccess) e = cudaEventRecord(ev[q++], c->stream);
     }
   }

@@ -143,6 +143,7 @@ struct Buffers {
   double* fixed;      // replay sequence
   double* acc;        // energy accumulators
   float* out;         // field/torque output for getters
+  float* part;        // row-stage path: the earlier-stage sums of a row kernel (k_rs_partial)
 };
 
 // enabled field terms; dmi is set by the library when a region has D != 0
@@ -219,9 +220,14 @@ void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m);
 
 // fused RK45 stage kernels (rowstage.cu): kind 0 = stage-input prep of stage
 // s, kind 1 = row kernel of stage s (mode 0 first stage only, 1 next stage,
-// 2 last stage with error and controller); maps from rowstage_maps
+// 2 last stage with error and controller); maps from rowstage_maps.  With
+// b.part set, the row kernels of modes 1 and 2 read their earlier-stage sums
+// from it: launch_rs_partial for the same (s, mode) must complete first.
 void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
                      double freq, double phase, cudaStream_t st);
+// the earlier-stage sums of the row kernel of stage s into b.part: mode 1
+// m + sum_{j<s} a_{s+1,j} k_j, mode 2 sum_{j<6} e_j k_j (needs k_0 .. k_{s-1})
+void launch_rs_partial(const Geom& g, const Buffers& b, int s, int mode, cudaStream_t st);
 // kernel spectrum octant: fills b.kt (float64 work inside); returns cudaError
 cudaError_t build_kernel_spectrum(const Geom& g, double dx, double dy, double dz, float* kt,
                                   cudaStream_t s);

@@ -14,9 +14,14 @@
 //              shared memory) -> effective field and LL torque k_s of its
 //              cells -> next stage input m_{s+1} and its x R2C, or, after the
 //              last stage, the error estimate, the candidate m and (last
-//              block) the step controller (Sec. IV).
+//              block) the step controller (Sec. IV);
+//   k_rs_partial  the part of that stage input (or error estimate) without
+//              k_s, an elementwise sum over m and the earlier k's that runs
+//              beside the (y, z) part of stage s, so that the row kernel
+//              reads one array instead of up to six.
 // Stage inputs alternate between two buffers (ms for even stages, ms2 for odd
 // ones), because a stage's stencil reads neighbours owned by other blocks.
+#include <algorithm>
 #include <cstring>
 
 #include "fft.cuh"
@@ -382,54 +387,60 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   if constexpr (!TT) stage_stencil<L, ROWS, NT>(g, ms, b.code, sten, scode, y0, z);
   const int par = st->parity;
-  const float* __restrict__ m = par ? p.m1 : p.m0;
   const int n = (int)g.n;
-  // 1. sums over the earlier stages at the block's cells, read from global
-  //    memory while the asynchronous copies are in flight: next stage
-  //    m + dt sum_j a_{s+1,j} k_j, or the error sum dt sum_j e_j k_j.  The
-  //    stage loop is unrolled (a zero coefficient skips its loads) so that all
-  //    loads of a cell are issued before the first is used.
-  float cj[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j)
-    cj[j] = mode == ROW_NEXT ? (j < s ? sc->ah[s + 1][j] : 0.f) : (mode == ROW_LAST ? sc->eh[j] : 0.f);
+  // 1. the earlier-stage sums at the block's cells: next stage
+  //    m + dt sum_{j<s} a_{s+1,j} k_j, or the error dt sum_{j<6} e_j k_j.
+  //    With b.part they come from k_rs_partial (a graph branch beside the
+  //    (y, z) part; loaded below, after the dependency wait, while the
+  //    spectrum copy is in flight); otherwise they are summed here from
+  //    global memory while the asynchronous copies are in flight, the stage
+  //    loop unrolled (a zero coefficient skips its loads) so that all loads
+  //    of a cell are issued before the first is used.  Same operation order
+  //    on both paths.
   float av[CPT][3];
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) {
-    const int e = threadIdx.x + q * NT;
-    av[q][0] = av[q][1] = av[q][2] = 0.f;
-    if (mode == ROW_K1 || e >= NCELL) continue;
-    const int x = e % L, r = e / L, y = y0 + r;
-    if (x >= g.nx || y >= g.ny) continue;
-    const int i = (z * g.ny + y) * g.nx + x;
-    float kj[6][3];
+  for (int q = 0; q < CPT; ++q) av[q][0] = av[q][1] = av[q][2] = 0.f;
+  if (!b.part && mode != ROW_K1) {
+    float cj[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      kj[j][0] = kj[j][1] = kj[j][2] = 0.f;
-      if (cj[j] != 0.0f) {
-        const float* __restrict__ k = pick_k(p, k_role(j, par));
-        kj[j][0] = k[i];
-        kj[j][1] = k[n + i];
-        kj[j][2] = k[2 * n + i];
-      }
-    }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    if (mode == ROW_NEXT) {
-      a0 = m[i];
-      a1 = m[n + i];
-      a2 = m[2 * n + i];
-    }
+    for (int j = 0; j < 6; ++j) cj[j] = mode == ROW_NEXT ? (j < s ? sc->ah[s + 1][j] : 0.f) : sc->eh[j];
+    const float* __restrict__ m = par ? p.m1 : p.m0;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      if (cj[j] != 0.0f) {
-        a0 = fmaf(cj[j], kj[j][0], a0);
-        a1 = fmaf(cj[j], kj[j][1], a1);
-        a2 = fmaf(cj[j], kj[j][2], a2);
+    for (int q = 0; q < CPT; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e >= NCELL) continue;
+      const int x = e % L, r = e / L, y = y0 + r;
+      if (x >= g.nx || y >= g.ny) continue;
+      const int i = (z * g.ny + y) * g.nx + x;
+      float kj[6][3];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        kj[j][0] = kj[j][1] = kj[j][2] = 0.f;
+        if (cj[j] != 0.0f) {
+          const float* __restrict__ k = pick_k(p, k_role(j, par));
+          kj[j][0] = k[i];
+          kj[j][1] = k[n + i];
+          kj[j][2] = k[2 * n + i];
+        }
       }
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      if (mode == ROW_NEXT) {
+        a0 = m[i];
+        a1 = m[n + i];
+        a2 = m[2 * n + i];
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (cj[j] != 0.0f) {
+          a0 = fmaf(cj[j], kj[j][0], a0);
+          a1 = fmaf(cj[j], kj[j][1], a1);
+          a2 = fmaf(cj[j], kj[j][2], a2);
+        }
+      }
+      av[q][0] = a0;
+      av[q][1] = a1;
+      av[q][2] = a2;
     }
-    av[q][0] = a0;
-    av[q][1] = a1;
-    av[q][2] = a2;
   }
   // the spectrum is the previous kernel's output (programmatic dependent
   // launch: everything above overlaps its last blocks)
@@ -448,6 +459,20 @@ __global__ void __launch_bounds__(NT, 2) k_rs_row(Geom g, Buffers b, Terms T, Pt
       else *dst = make_float2(0.f, 0.f);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  // (1. continued: the precomputed sums, used after the field)
+  if (b.part && mode != ROW_K1) {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e >= NCELL) continue;
+      const int x = e % L, r = e / L, y = y0 + r;
+      if (x >= g.nx || y >= g.ny) continue;
+      const int i = (z * g.ny + y) * g.nx + x;
+      av[q][0] = b.part[i];
+      av[q][1] = b.part[n + i];
+      av[q][2] = b.part[2 * n + i];
+    }
   }
   // 2. x C2R of the demag spectrum rows (3 components); the output is in
   //    rows of pitch L + 1 (layout B) on both paths
@@ -690,6 +715,58 @@ Ptrs rs_ptrs(const Buffers& b) {
   return p;
 }
 
+// Earlier-stage sums of the row kernel of stage s, elementwise over the 3 n
+// values of the component-major arrays (16-byte vectors, then the tail):
+// ROW_NEXT  P = m + sum_{j<s} a_{s+1,j} k_j   (the next stage input of the
+//           Dormand-Prince tableau without its k_s term, Sec. IV),
+// ROW_LAST  P = sum_{j<6} e_j k_j             (the error estimate without k_6),
+// the coefficients carrying dt; m first, then j ascending, one fused
+// multiply-add each (the row kernel adds the k_s term).  It reads only
+// k_0 .. k_{s-1}, all complete once the row kernel of stage s - 1 is, and
+// runs as a graph branch beside the (y, z) part of stage s.
+constexpr int kPartNT = 256;
+
+__global__ void __launch_bounds__(kPartNT) k_rs_partial(float* __restrict__ out, Ptrs p,
+                                                        const DevState* __restrict__ st,
+                                                        const StageCoef* __restrict__ sc, int s, int mode, int n3) {
+  if (st->done) return;
+  const int par = st->parity;
+  float cj[6];
+  const float* kp[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    cj[j] = mode == ROW_NEXT ? (j < s ? sc->ah[s + 1][j] : 0.f) : sc->eh[j];
+    kp[j] = pick_k(p, k_role(j, par));
+  }
+  const float* __restrict__ m = mode == ROW_NEXT ? (par ? p.m1 : p.m0) : nullptr;
+  const int n4 = n3 >> 2, stride = gridDim.x * kPartNT;
+  for (int e = blockIdx.x * kPartNT + threadIdx.x; e < n4; e += stride) {
+    // (every load of the element issued before the first use)
+    float4 v[6];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a = m ? reinterpret_cast<const float4*>(m)[e] : z4;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = cj[j] != 0.0f ? reinterpret_cast<const float4*>(kp[j])[e] : z4;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (cj[j] != 0.0f) {
+        a.x = fmaf(cj[j], v[j].x, a.x);
+        a.y = fmaf(cj[j], v[j].y, a.y);
+        a.z = fmaf(cj[j], v[j].z, a.z);
+        a.w = fmaf(cj[j], v[j].w, a.w);
+      }
+    }
+    reinterpret_cast<float4*>(out)[e] = a;
+  }
+  for (int e = 4 * n4 + blockIdx.x * kPartNT + threadIdx.x; e < n3; e += stride) {
+    float a = m ? m[e] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (cj[j] != 0.0f) a = fmaf(cj[j], kp[j][e], a);
+    out[e] = a;
+  }
+}
+
 // ROWS * L = 1024 points per block, or 256 when that leaves too few blocks.
 // Threads: one per radix-8 butterfly of the three components' rows (at
 // least one per cell up to 256 was measured slower on the 256 x 256 film:
@@ -880,6 +957,18 @@ void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m) {
     }
     m->ok_sten = ok ? 1 : 0;
   }
+}
+
+// Up to two blocks per multiprocessor: the kernel shares the GPU with the
+// (y, z) kernels of the same stage and has their whole duration to finish.
+void launch_rs_partial(const Geom& g, const Buffers& b, int s, int mode, cudaStream_t st) {
+  const int n3 = 3 * (int)g.n;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  const int blocks = std::max(1, std::min((n3 / 4 + kPartNT - 1) / kPartNT, 2 * sms));
+  StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
+  k_rs_partial<<<blocks, kPartNT, 0, st>>>(b.part, rs_ptrs(b), b.st, sc, s, mode, n3);
 }
 
 // kind 0: prep of stage s; kind 1: row kernel of stage s with mode 0 (first

@@ -173,7 +173,7 @@ def fp32_peak(device=0, reps=5):
     return tf.value, sms.value, mhz.value
 
 
-KERNEL_KINDS = {0: "prep", 1: "yz", 2: "row", 3: "yf", 4: "zk", 5: "yi"}
+KERNEL_KINDS = {0: "prep", 1: "yz", 2: "row", 3: "yf", 4: "zk", 5: "yi", 6: "part"}
 
 
 class Context:
