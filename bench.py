@@ -204,19 +204,32 @@ def yz_kernel_bytes(p):
     return fused, floor
 
 
-def row_kernel_bytes(p):
+# arrays the earlier-stage sums of the six row kernels read (m + the k's with
+# a nonzero Dormand-Prince coefficient; the last: the error's 5 k's)
+EARLIER_ARRAYS = [2, 3, 4, 5, 5, 5]
+
+
+def row_kernel_bytes(p, partial=False):
     """Algorithmic HBM bytes of one row-stage kernel launch, the mean over the
     six launches of an attempt: read the demag spectrum rows and the stage
     input (its stencil neighbours are the same array) and the cell codes,
-    read m and the earlier stages' k the Dormand-Prince rows need (2, 3, 4,
-    5, 5 arrays for stages 2..6 with m; 5 k's for the error of the last),
-    write k_s, and the next stage input and its spectrum rows (stages 2..6)
-    or the candidate m (the last): 69 MB at 128 x 128 x 32."""
+    read the earlier-stage sums' inputs (m and the earlier k's: 2, 3, 4, 5, 5
+    arrays for stages 2..6, 5 k's for the error of the last; with `partial`
+    the one array k_rs_partial made of them), write k_s, and the next stage
+    input and its spectrum rows (stages 2..6) or the candidate m (the last):
+    69 MB at 128 x 128 x 32, 51 MB with `partial`."""
     arr = 12 * p.ncells                      # one float32 3-vector field
     spec = _spectrum_rows_bytes(p)
-    earlier = [2, 3, 4, 5, 5, 5]             # arrays read per launch (m + k's; the last: 5 k's)
+    earlier = [1] * 6 if partial else EARLIER_ARRAYS
     per = [spec + arr + 4 * p.ncells + e * arr + arr + (arr + spec if i < 5 else arr) for i, e in enumerate(earlier)]
     return sum(per) / len(per)
+
+
+def partial_kernel_bytes(p):
+    """Algorithmic HBM bytes of one k_rs_partial launch, the mean over the six
+    of an attempt: read m and the earlier k's, write one array."""
+    arr = 12 * p.ncells
+    return sum((e + 1) * arr for e in EARLIER_ARRAYS) / len(EARLIER_ARRAYS)
 
 
 def algorithmic_demag_flops(p):
@@ -485,11 +498,21 @@ def run_ours(args, rank, world, local_rank):
     roofline_row = None
     if "row" in per_kind:
         t_row = per_kind["row"]["mean_us"] * 1e-6
-        rb = row_kernel_bytes(p)
+        branch = "part" in per_kind
+        rb = row_kernel_bytes(p, partial=branch)
         roofline_row = {"bound": "hbm", "achieved": round(rb / t_row / 1e9, 1), "peak": peaks["hbm_gbs"],
                         "unit": "GB/s", "frac": round(rb / t_row / 1e9 / peaks["hbm_gbs"], 4),
-                        "kernel": "row-stage kernel k_rs_row (x C2R, field, torque, stage update, x R2C)",
+                        "kernel": "row-stage kernel k_rs_row (x C2R, field, torque, stage update, x R2C)"
+                                  + (", earlier-stage sums read from k_rs_partial" if branch else ""),
                         "algorithmic_bytes": rb, "avg_launch_us": round(t_row * 1e6, 2)}
+        if branch:
+            t_part = per_kind["part"]["mean_us"] * 1e-6
+            pb = partial_kernel_bytes(p)
+            roofline_row["partial"] = {
+                "kernel": "k_rs_partial (earlier-stage sums; a graph branch beside the (y, z) part)",
+                "algorithmic_bytes": pb, "avg_launch_us": round(t_part * 1e6, 2),
+                "achieved": round(pb / t_part / 1e9, 1),
+                "frac": round(pb / t_part / 1e9 / peaks["hbm_gbs"], 4)}
     step_kernels = {"per_kind": per_kind,
                     "sum_us_per_attempt": round(sum(us for _, us in prof), 1),
                     "graph_us_per_attempt": round(t_max / max(attempts, 1) * 1e6, 1),
@@ -512,7 +535,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     conv_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / R
     five = five_pass_demag_bytes(p)
-    convolution = {"kernels": "k_fx_t + k_yz2 + k_ix_t (mm_demag_apply), L2 flushed before each call",
+    convolution = {"kernels": "x R2C (k_fx_t) + the context's (y, z) part + x C2R (k_ix_t) "
+                              "(mm_demag_apply), L2 flushed before each call",
                    "avg_us": round(conv_s * 1e6, 2), "five_pass_bytes": five,
                    "five_pass_equiv_gbs": round(five / conv_s / 1e9, 1),
                    "five_pass_equiv_frac": round(five / conv_s / 1e9 / peaks["hbm_gbs"], 4),
