@@ -71,18 +71,21 @@ __global__ void k_torque(Geom g, Buffers b, Terms T, Stt S, Ptrs p, const DevSta
 
 __global__ void k_begin(DevState* st, StageCoef* sc, const double* __restrict__ fixed, int mode, long long nsteps,
                         double t_end) {
-  st->status = 0;
-  st->done = 0;
-  st->call_attempts = 0;
-  st->err_bits = 0;
-  st->ticket = 0;
-  st->mode = mode;
-  st->target = st->accepted + nsteps;
-  st->t_end = t_end;
-  if (mode == 2 && st->fixed_idx >= st->fixed_n) st->done = 1;
-  check_done(st);
-  if (nsteps <= 0 && mode != 1) st->done = 1;
-  if (!st->done) prepare_attempt(st, sc, fixed);
+  // (on a local copy: one bulk read and one bulk write of the state)
+  DevState s = *st;
+  s.status = 0;
+  s.done = 0;
+  s.call_attempts = 0;
+  s.err_bits = 0;
+  s.ticket = 0;
+  s.mode = mode;
+  s.target = s.accepted + nsteps;
+  s.t_end = t_end;
+  if (mode == 2 && s.fixed_idx >= s.fixed_n) s.done = 1;
+  check_done(&s);
+  if (nsteps <= 0 && mode != 1) s.done = 1;
+  if (!s.done) prepare_attempt(&s, sc, fixed);
+  *st = s;
 }
 
 // error estimate, candidate m (normalised 5th-order solution), block max,

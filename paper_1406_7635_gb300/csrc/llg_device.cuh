@@ -316,8 +316,8 @@ __device__ void check_done(DevState* st) {
 // whose error estimate is of order 2), bounded by dt_max, and
 // at least dt_min after an accepted step; a rejection that would need a step
 // below dt_min ends the call with MM_ERR_DT_UNDERFLOW.
-__device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ hist,
-                           const double* __restrict__ fixed) {
+__device__ void controller_on(DevState* st, StageCoef* sc, double* __restrict__ hist,
+                              const double* __restrict__ fixed) {
   const double eps = (double)__uint_as_float(st->err_bits);
   st->err_bits = 0;
   st->ticket = 0;
@@ -355,6 +355,18 @@ __device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ his
     st->dt = ndt;
   }
   if (!st->done) prepare_attempt(st, sc, fixed);
+}
+
+// The controller on a local copy of the device state: one bulk read (all of
+// its loads in flight at once) and one bulk write, instead of a chain of
+// single-field round trips through memory on the attempt's critical path.
+// It runs in one thread after every other block of the attempt has finished
+// with the state.
+__device__ void controller(DevState* st, StageCoef* sc, double* __restrict__ hist,
+                           const double* __restrict__ fixed) {
+  DevState s = *st;
+  controller_on(&s, sc, hist, fixed);
+  *st = s;
 }
 
 }  // namespace
