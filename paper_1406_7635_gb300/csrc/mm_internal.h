@@ -224,7 +224,7 @@ void rowstage_maps(const Geom& g, const Buffers& b, RsMaps* m);
 // b.part set, the row kernels of modes 1 and 2 read their earlier-stage sums
 // from it: launch_rs_partial for the same (s, mode) must complete first.
 void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
-                     double freq, double phase, cudaStream_t st);
+                     double freq, double phase, cudaStream_t st, bool dep = false);
 // the earlier-stage sums of the row kernel of stage s into b.part: mode 1
 // m + sum_{j<s} a_{s+1,j} k_j, mode 2 sum_{j<6} e_j k_j (needs k_0 .. k_{s-1})
 void launch_rs_partial(const Geom& g, const Buffers& b, int s, int mode, cudaStream_t st);

@@ -780,7 +780,7 @@ struct RsCfg {
 
 template <int L, int ROWS, bool SL, bool SS, bool TT>
 void launch_row(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int s, int mode, double freq,
-                double ph, cudaStream_t st) {
+                double ph, cudaStream_t st, bool dep) {
   using C = RsCfg<L, ROWS>;
   StageCoef* sc = reinterpret_cast<StageCoef*>(b.st + 1);
   cudaLaunchConfig_t cfg = {};
@@ -790,7 +790,7 @@ void launch_row(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& m
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = pdl_row(g) ? 1 : 0;
+  attr[0].val.programmaticStreamSerializationAllowed = dep ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_rs_row<L, ROWS, C::NT, SL, SS, TT>, g, b, T, rs_ptrs(b), b.st, sc, s, mode, freq, ph,
@@ -799,7 +799,7 @@ void launch_row(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& m
 
 template <int L, int ROWS>
 void launch_rs(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
-               double freq, double phase, cudaStream_t st) {
+               double freq, double phase, cudaStream_t st, bool dep) {
   using C = RsCfg<L, ROWS>;
   constexpr bool SPEC = rs_spec_shape<L, ROWS>(), STEN = rs_sten_shape<L>();
   const bool spec = SPEC && maps.ok_spec, sten = STEN && maps.ok_sten;
@@ -817,12 +817,12 @@ void launch_rs(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& ma
     return;
   }
   if constexpr (SPEC && STEN) {
-    if (spec && sten) return launch_row<L, ROWS, kRsSL, kRsSS, kRsTT>(g, b, T, maps, s, mode, freq, ph, st);
+    if (spec && sten) return launch_row<L, ROWS, kRsSL, kRsSS, kRsTT>(g, b, T, maps, s, mode, freq, ph, st, dep);
   }
   if constexpr (STEN) {
-    if (sten) return launch_row<L, ROWS, false, false, kRsTT>(g, b, T, maps, s, mode, freq, ph, st);
+    if (sten) return launch_row<L, ROWS, false, false, kRsTT>(g, b, T, maps, s, mode, freq, ph, st, dep);
   }
-  launch_row<L, ROWS, false, false, false>(g, b, T, maps, s, mode, freq, ph, st);
+  launch_row<L, ROWS, false, false, false>(g, b, T, maps, s, mode, freq, ph, st, dep);
 }
 
 template <int L, int ROWS, bool SL, bool SS, bool TT>
@@ -853,9 +853,9 @@ struct RsRows {
 
 template <int L>
 void launch_rs_l(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
-                 double freq, double phase, cudaStream_t st) {
-  if (RsRows<L>::big(g)) launch_rs<L, RsRows<L>::R1>(g, b, T, maps, kind, s, mode, freq, phase, st);
-  else launch_rs<L, RsRows<L>::R2>(g, b, T, maps, kind, s, mode, freq, phase, st);
+                 double freq, double phase, cudaStream_t st, bool dep) {
+  if (RsRows<L>::big(g)) launch_rs<L, RsRows<L>::R1>(g, b, T, maps, kind, s, mode, freq, phase, st, dep);
+  else launch_rs<L, RsRows<L>::R2>(g, b, T, maps, kind, s, mode, freq, phase, st, dep);
 }
 
 template <int L>
@@ -972,16 +972,19 @@ void launch_rs_partial(const Geom& g, const Buffers& b, int s, int mode, cudaStr
 }
 
 // kind 0: prep of stage s; kind 1: row kernel of stage s with mode 0 (first
-// stage only), 1 (next stage), 2 (last stage: error and controller)
+// stage only), 1 (next stage), 2 (last stage: error and controller); the row
+// kernel is a programmatic dependent of its predecessor where pdl_row(g) or
+// `dep` says so
 void launch_rowstage(const Geom& g, const Buffers& b, const Terms& T, const RsMaps& maps, int kind, int s, int mode,
-                     double freq, double phase, cudaStream_t st) {
+                     double freq, double phase, cudaStream_t st, bool dep) {
+  dep = dep || pdl_row(g);
   switch (g.lx) {
-    case 16: launch_rs_l<16>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
-    case 32: launch_rs_l<32>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
-    case 64: launch_rs_l<64>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
-    case 128: launch_rs_l<128>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
-    case 256: launch_rs_l<256>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
-    case 512: launch_rs_l<512>(g, b, T, maps, kind, s, mode, freq, phase, st); break;
+    case 16: launch_rs_l<16>(g, b, T, maps, kind, s, mode, freq, phase, st, dep); break;
+    case 32: launch_rs_l<32>(g, b, T, maps, kind, s, mode, freq, phase, st, dep); break;
+    case 64: launch_rs_l<64>(g, b, T, maps, kind, s, mode, freq, phase, st, dep); break;
+    case 128: launch_rs_l<128>(g, b, T, maps, kind, s, mode, freq, phase, st, dep); break;
+    case 256: launch_rs_l<256>(g, b, T, maps, kind, s, mode, freq, phase, st, dep); break;
+    case 512: launch_rs_l<512>(g, b, T, maps, kind, s, mode, freq, phase, st, dep); break;
     default: break;
   }
 }
