@@ -2,9 +2,11 @@
 // [c][kx][z][y]): per attempt, one prep kernel and, per stage, the y/z
 // transform kernel (k_yz2 / k_yz) plus one row kernel, instead of five
 // kernels per stage.  Where the shape allows, the row kernel moves its
-// spectrum box and stencil rows with tensor copies (TMA), and on grids with
-// the z-split y/z kernel it is launched as a programmatic dependent of it
-// (its stencil copies and earlier-stage sums run before the wait).
+// spectrum box and stencil rows with tensor copies (TMA).  On 3-D grids with
+// the z-split (y, z) part and on 2-D grids with the one-kernel (y, z) path it
+// is launched as a programmatic dependent of its predecessor: its stencil
+// copies, table loads and (where they are summed in the kernel) earlier-stage
+// sums run before the wait.
 //
 // A block owns ROWS complete x-rows (one z plane) of all three components.
 //   k_rs_prep  stage input m_s = m + dt sum_j a_sj k_j for its cells, written

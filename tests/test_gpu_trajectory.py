@@ -95,3 +95,21 @@ def test_ellipsoid_twenty_steps_replayed(mm):
     err = float(np.abs(m_gpu - ora.m).max())
     print(f"\n128x128x32 ellipsoid, 20 replayed steps: max |m_gpu - m_oracle| = {err:.3e}")
     assert err <= M_TOL
+
+
+def test_grain_film_twenty_steps_replayed(mm):
+    """The 256 x 256 x 1 grain film on its default path (the one-kernel 2-D
+    (y, z) part with the row kernel started as its programmatic dependent):
+    20 accepted steps replayed by the oracle."""
+    p = WORKLOADS["grains_256x256x1"]()
+    ctx = mm.Context.from_problem(p)
+    ctx.step(20)
+    m_gpu = ctx.get_m().astype(np.float64)
+    dts = ctx.get_dt_history()
+    ctx.close()
+    assert len(dts) == 20
+    ora = RK45(p, m=p.m0.astype(np.float32).astype(np.float64))
+    ora.run_fixed(dts)
+    err = float(np.abs(m_gpu - ora.m).max())
+    print(f"\n256x256x1 grain film, 20 replayed steps: max |m_gpu - m_oracle| = {err:.3e}")
+    assert err <= M_TOL
