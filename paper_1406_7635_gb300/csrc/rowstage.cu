@@ -245,7 +245,10 @@ struct RsSmem {
 // and the prep kernel's spectrum store (PS).  Measured on the 128 x 128 x 32
 // step (same GPU, ms per step): all four 0.5516, PS off 0.5472, SS and PS off
 // 0.5485, TT off 0.5643; the prep kernel's blocks are short and waiting for
-// their store to drain costs more than the scattered stores.
+// their store to drain costs more than the scattered stores.  Re-measured
+// with the current (y, z) kernels and the earlier-stage sums branch: PS on
+// makes the prep kernel 15.5 -> 14.6 us and leaves the step where it is
+// (0.433-0.435 ms either way), so it stays off.
 constexpr bool kRsSL = true;
 constexpr bool kRsSS = true;
 constexpr bool kRsTT = true;
