@@ -176,7 +176,9 @@ __device__ void b_controller(InstState& s, double* __restrict__ hist) {
     return;
   }
   const double h = s.h;
-  const double factor = eps == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, s.headroom * pow(s.max_err / eps, 0.2)));
+  // (the growth factor in float32, as in the single-context controller)
+  const float ratio = (float)s.max_err / (float)eps;
+  const double factor = eps == 0.0 ? 5.0 : (double)fminf(5.0f, fmaxf(0.2f, (float)s.headroom * powf(ratio, 0.2f)));
   const double ndt = fmin(h * factor, s.dt_max);
   if (eps <= s.max_err) {
     s.t += h;
