@@ -88,11 +88,12 @@ struct Geom {
 // Programmatic dependent launch of the RK stage kernels: a kernel launched
 // with it may start on free SMs while its predecessor drains, and waits for
 // the predecessor's results with grid_dependency_wait() before reading them.
-// Per geometry, from same-GPU measurements (ms per step, none / row / y-z /
-// both): 128 x 128 x 32 (z-split y/z kernel, 1.7 waves of large blocks)
-// 0.549 / 0.535 / 0.549 / 0.550; 256 x 256 x 1 film (one wave) 0.165 / 0.197
-// / 0.161 / 0.203.  The row kernel's stencil copies and earlier-stage sums
-// only gain where they fill the y/z kernel's last wave.
+// With the cluster (y, z) kernel, per geometry, from same-GPU measurements
+// (ms per step, none / row / y-z / both): 128 x 128 x 32 (z-split y/z kernel,
+// 1.7 waves of large blocks) 0.549 / 0.535 / 0.549 / 0.550; 256 x 256 x 1 film
+// (one wave) 0.165 / 0.197 / 0.161 / 0.203.  The register-resident (y, z)
+// kernels of fft_yz3.cu are always dependents; behind the one-kernel 2-D path
+// the context also makes the row kernel one (launch_rowstage's `dep`).
 inline bool pdl_row(const Geom& g) { return g.fused && g.clz == 2; }
 inline bool pdl_yz(const Geom& g) { return !pdl_row(g); }
 
